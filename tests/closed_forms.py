@@ -1,0 +1,85 @@
+"""Closed forms of what the workload programs compute, written directly with numpy.
+
+They restate each program's intent on the event arrays (no eBPF involved), so they pin
+both the oracle and, at sizes the oracle cannot reach quickly, the engine:
+  counting  -> bincount of event.kind
+  page_heat -> group-by of addr >> 21: (sum of weights, max timestamp); per-kind tally
+  latency   -> 2-D histogram of (kernel id, floor(log2(latency))); outliers latency > T
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Tuple
+
+import numpy as np
+
+from workloads import programs as P
+
+
+def counting(ev: np.ndarray, n_counters: int = 256) -> np.ndarray:
+    k = ev["kind"].astype(np.int64)
+    ok = (ev["size"] != 0) & (k < n_counters)
+    return np.bincount(k[ok], minlength=n_counters).astype(np.uint64)
+
+
+def popcount8(x: np.ndarray) -> np.ndarray:
+    x = x & 0xFF
+    c = np.zeros_like(x)
+    for b in range(8):
+        c += (x >> b) & 1
+    return c
+
+
+def page_heat(ev: np.ndarray) -> Tuple[Dict[int, Tuple[int, int]], np.ndarray]:
+    """({region: (count, last_ts)}, tally[16, 2]) for records the program accepts."""
+    addr, size, kind, ts = ev["addr"], ev["size"].astype(np.uint64), ev["kind"].astype(np.uint64), ev["ts_ns"]
+    pow2 = (size != 0) & (size <= 4096) & ((size & (size - np.uint64(1))) == 0)
+    ok = pow2 & (kind < 8)
+    tally = np.zeros((P.PAGE_HEAT_TALLY, 2), dtype=np.uint64)
+    tally[8, 0] = np.count_nonzero(~ok)
+    a, s, k, t = addr[ok], size[ok], kind[ok], ts[ok]
+    mis = (a & (s - np.uint64(1))) != 0
+    tally[9, 0] = np.count_nonzero(mis)
+    tally[:8, 0] = np.bincount(k.astype(np.int64), minlength=8)[:8]
+    tally[:8, 1] = np.bincount(k.astype(np.int64), weights=s.astype(np.float64), minlength=8)[:8].astype(np.uint64)
+    w = np.uint64(1) + popcount8(a >> np.uint64(12))
+    region = a >> np.uint64(21)
+    order = np.argsort(region, kind="stable")
+    r_sorted = region[order]
+    uniq, starts = np.unique(r_sorted, return_index=True)
+    sums = np.add.reduceat(w[order], starts)
+    maxts = np.maximum.reduceat(t[order], starts)
+    heat = {int(u): (int(c), int(m)) for u, c, m in zip(uniq, sums, maxts)}
+    return heat, tally
+
+
+def floor_log2(x: np.ndarray) -> np.ndarray:
+    b = np.zeros(x.shape, dtype=np.int64)
+    for k in range(1, 64):
+        b += (x >> np.uint64(k)) > 0
+    return b
+
+
+def latency(ev: np.ndarray, n_kernels: int = 4096, threshold: int | None = None):
+    """(hist[n_kernels*64] u64, outliers [(pair index, payload bytes)] in index order)."""
+    if threshold is None:
+        import math
+        threshold = P.lognormal_quantile_ns(math.log(20000.0), 1.0, 0.99)
+    e, x = ev[0::2], ev[1::2]
+    kid = (e["addr"] & np.uint64(0xFFFFFFFF))
+    ok = (e["kind"] == 0) & (x["kind"] == 1) & ((x["addr"] & np.uint64(0xFFFFFFFF)) == kid)
+    ok &= kid < n_kernels
+    ok &= x["ts_ns"] >= e["ts_ns"]
+    lat = (x["ts_ns"] - e["ts_ns"])
+    b = floor_log2(lat)
+    idx = kid[ok].astype(np.int64) * P.LAT_BUCKETS + b[ok]
+    hist = np.bincount(idx, minlength=n_kernels * P.LAT_BUCKETS).astype(np.uint64)
+    out: List[Tuple[int, bytes]] = []
+    sel = np.nonzero(ok & (lat > np.uint64(threshold)))[0]
+    for i in sel:
+        rec = np.zeros(1, dtype=[("addr", "<u8"), ("kid", "<u4"), ("bucket", "<u4"), ("ets", "<u8"), ("xts", "<u8"),
+                                 ("lat", "<u8"), ("sm", "<u4"), ("warp", "<u4")])
+        rec["addr"], rec["kid"], rec["bucket"] = e["addr"][i], kid[i], b[i]
+        rec["ets"], rec["xts"], rec["lat"] = e["ts_ns"][i], x["ts_ns"][i], lat[i]
+        rec["sm"], rec["warp"] = e["sm_id"][i], e["warp_id"][i]
+        out.append((int(i), rec.tobytes()))
+    return hist, out
