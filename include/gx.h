@@ -1,0 +1,308 @@
+/*
+ * gx -- a device-side eBPF execution engine for one GB300 GPU (sm_103a).
+ *
+ * The engine runs verified eBPF policy and observability programs over large batches
+ * of device-resident event records, with array maps, lock-free hash maps and a ring
+ * buffer kept in device memory.  It is the data-parallel core of the device-side eBPF
+ * runtime of "gpu_ext: Extensible OS Policies for GPUs via eBPF" (arXiv 2512.12615):
+ *   - device program type with a compact read-only context (Sec. 4.3, Sec. 4.3.1);
+ *   - verification before execution: typed registers, bounded loops, memory safety,
+ *     per-hook resource budgets (Sec. 4.4, Sec. 4.4.1, Sec. 5.3);
+ *   - warp-level aggregated map updates (Sec. 4.4.2, Sec. 5.3 "Hierarchical Maps");
+ *   - maps as the shared key-value state, snapshotted at kernel completion (Sec. 4.4.3);
+ *   - persistent workers claiming logical work units (Sec. 4.3.2, Sec. 5.3).
+ * Instruction semantics follow the standard eBPF ISA (RFC 9669); map helpers use the
+ * Linux UAPI helper numbers and return codes.
+ *
+ * Conventions for every entry point below:
+ *   - return 0 on success or a negative status (GX_E*; errno values where one exists);
+ *   - pointers named *_dev are device pointers owned by the caller and must stay valid
+ *     until the work on `stream` completes; *_host pointers are host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream);
+ *   - asynchronous calls only enqueue work; gx_last_status, gx_map_read and
+ *     gx_ringbuf_drain synchronise `stream`;
+ *   - device-side errors never trap: they are recorded in a sticky status word that
+ *     gx_last_status returns;
+ *   - objects are not thread-safe: one host thread drives a given context at a time
+ *     (the server object below is the exception and documents its own rules).
+ */
+#ifndef GX_H
+#define GX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define GX_OK 0
+#define GX_ENOENT (-2)
+#define GX_E2BIG (-7)
+#define GX_EAGAIN (-11)
+#define GX_ENOMEM (-12)
+#define GX_EFAULT (-14)
+#define GX_EEXIST (-17)
+#define GX_EINVAL (-22)
+#define GX_ENOSPC (-28)
+#define GX_E_VERIFY (-1000)    /* program rejected by the verifier; see the log */
+#define GX_E_CUDA (-1001)      /* a CUDA runtime call failed */
+#define GX_E_BUDGET (-1002)    /* an event exceeded its dynamic instruction budget */
+#define GX_E_TIMEOUT (-1003)   /* a bounded device wait gave up */
+#define GX_E_DEVICE (-1004)    /* device-side invariant violated (sticky status) */
+#define GX_E_ADMISSION (-1005) /* request larger than the server's memory budget */
+#define GX_E_NODEV (-1006)     /* no CUDA device or wrong architecture */
+
+/* ---------------------------------------------------------------- map types (Linux enum values) */
+#define GX_MAP_HASH 1
+#define GX_MAP_ARRAY 2
+#define GX_MAP_RINGBUF 27
+
+/* map update flags (Linux BPF_ANY / BPF_NOEXIST / BPF_EXIST) */
+#define GX_ANY 0
+#define GX_NOEXIST 1
+#define GX_EXIST 2
+
+/* helper ids usable in CALL instructions */
+#define GX_HELPER_MAP_LOOKUP 1
+#define GX_HELPER_MAP_UPDATE 2
+#define GX_HELPER_MAP_DELETE 3
+#define GX_HELPER_RINGBUF_OUTPUT 130
+#define GX_HELPER_RINGBUF_RESERVE 131
+#define GX_HELPER_RINGBUF_SUBMIT 132
+#define GX_HELPER_RINGBUF_DISCARD 133
+#define GX_HELPER_ATOMIC_MAX_U64 0x10000 /* void (u64 *p, u64 v): *p = max(*p, v) */
+#define GX_HELPER_ATOMIC_MIN_U64 0x10001 /* void (u64 *p, u64 v): *p = min(*p, v) */
+
+/* limits */
+#define GX_MAX_INSNS 4096
+#define GX_MAX_MAPS 16
+#define GX_STACK_BYTES 512
+#define GX_MAX_CTX 256
+#define GX_MAX_KEY 64
+#define GX_MAX_VALUE 4096
+
+typedef struct gx_ctx gx_ctx;
+typedef struct gx_map gx_map;
+typedef struct gx_prog gx_prog;
+typedef struct gx_batch gx_batch;
+typedef struct gx_server gx_server;
+
+/* ---------------------------------------------------------------- context */
+/*
+ * Open the engine on CUDA device `device`.  mem_budget: bytes of device memory the
+ * engine's own allocations (maps, program images, scratch) may use; 0 = no limit.
+ * Fails with GX_E_NODEV if the device is missing or not compute capability 10.3.
+ */
+int gx_init(int device, uint64_t mem_budget, gx_ctx **out);
+/* Destroy the context; every map, program, batch and server made from it must be
+ * destroyed first (GX_EINVAL otherwise).  Synchronises the device. */
+int gx_shutdown(gx_ctx *ctx);
+/* Bytes currently allocated by the engine on the device. */
+uint64_t gx_mem_used(const gx_ctx *ctx);
+/* Static text for a status code. */
+const char *gx_strerror(int status);
+
+/* ---------------------------------------------------------------- maps (Sec. 4.4.3) */
+/*
+ * Create a device-resident map.
+ *   GX_MAP_ARRAY:   key_size must be 4 (u32 index); value_size 1..GX_MAX_VALUE;
+ *                   max_entries >= 1; all values start at zero.
+ *   GX_MAP_HASH:    key_size 1..GX_MAX_KEY, value_size 1..GX_MAX_VALUE; lock-free open
+ *                   addressing over a power-of-two table of at least 2*max_entries slots;
+ *                   at most max_entries live keys (further inserts return -E2BIG);
+ *                   deleted slots are not reused until gx_map_clear.
+ *   GX_MAP_RINGBUF: key_size = value_size = 0; max_entries = buffer bytes (power of two,
+ *                   >= 4096).  Records are {u32 len; u32 flags; u64 event_idx} + payload
+ *                   padded to 8 bytes; the buffer fills from offset 0 until drained.
+ * flags: reserved, must be 0.
+ * Memory is taken from the context budget (GX_ENOMEM when exceeded).
+ */
+int gx_map_create(gx_ctx *ctx, uint32_t type, uint32_t key_size, uint32_t value_size, uint32_t max_entries,
+                  uint32_t flags, gx_map **out);
+/* Drop the caller's reference; the map is freed once no program references it. */
+int gx_map_destroy(gx_map *map);
+/* Device bytes held by the map. */
+uint64_t gx_map_bytes(const gx_map *map);
+
+/*
+ * Snapshot a map to host memory; synchronises `stream` (Sec. 4.4.3: snapshots at kernel
+ * completion boundaries).
+ *   array: max_entries * value_size bytes, entry i at offset i*value_size; *n_out = max_entries.
+ *   hash:  packed {key, value} pairs (key_size + value_size bytes each), in unspecified
+ *          order; *n_out = number of live pairs.  GX_E2BIG if cap_bytes is too small.
+ *   ringbuf: not allowed (use gx_ringbuf_drain).
+ */
+int gx_map_read(gx_map *map, void *host_out, uint64_t cap_bytes, uint64_t *n_out, void *stream);
+/*
+ * Restore a map from host memory (the inverse of gx_map_read); synchronises `stream`.
+ *   array: exactly max_entries*value_size bytes, overwriting every value.
+ *   hash:  packed {key, value} pairs, inserted or overwritten (BPF_ANY semantics);
+ *          GX_E2BIG if the live count would exceed max_entries.
+ */
+int gx_map_write(gx_map *map, const void *host_in, uint64_t bytes, void *stream);
+/* Reset to the empty state (zero values / no keys / empty ring, counters zeroed). Async. */
+int gx_map_clear(gx_map *map, void *stream);
+/*
+ * Copy the committed ring-buffer records to host memory and empty the ring; synchronises
+ * `stream`.  Discarded records are skipped; order is reservation order.  *bytes_out =
+ * bytes written, *dropped = reservations refused for lack of space since the last drain.
+ * GX_E2BIG (and nothing consumed) if cap is too small.
+ */
+int gx_ringbuf_drain(gx_map *rb, void *host_out, uint64_t cap, uint64_t *bytes_out, uint64_t *dropped,
+                     void *stream);
+
+/* ---------------------------------------------------------------- programs (Sec. 4.4, Sec. 5.3) */
+typedef struct gx_map_spec {
+    uint32_t type, key_size, value_size, max_entries;
+} gx_map_spec;
+
+typedef struct gx_prog_opts {
+    uint32_t ctx_size;      /* bytes of one event record: multiple of 8 in [8, GX_MAX_CTX] */
+    uint32_t deterministic; /* 1: also reject programs whose results could depend on event order */
+    uint64_t insn_budget;   /* per-event limit on taken backward jumps; 0 = 1<<16 */
+    uint32_t flags;         /* reserved, 0 */
+    uint32_t reserved;
+} gx_prog_opts;
+
+/*
+ * Verify `n_insns` raw eBPF slots (RFC 9669 encoding, little-endian) against map specs,
+ * on the host only (no device needed).  Returns 0 if accepted, GX_E_VERIFY if rejected,
+ * GX_EINVAL for bad arguments.  `log` (nullable) receives a NUL-terminated reason.
+ * Map references are LD_IMM64 with src_reg = 1 and imm = index into `maps`.
+ */
+int gx_verify(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+              const gx_prog_opts *opts, char *log, size_t log_len);
+/* Verify, decode and upload a program; it holds a reference on each map. */
+int gx_verify_load(gx_ctx *ctx, const uint64_t *insns, uint32_t n_insns, gx_map *const *maps, uint32_t n_maps,
+                   const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len);
+int gx_prog_destroy(gx_prog *prog);
+/* Number of device micro-ops the program decoded to. */
+uint32_t gx_prog_uops(const gx_prog *prog);
+
+/* ---------------------------------------------------------------- runs */
+typedef struct gx_launch {
+    uint32_t block; /* threads per block: 64..1024, multiple of 32; 0 = tuned/default */
+    uint32_t ept;   /* events per thread: 1..64; 0 = tuned/default */
+    uint32_t grid;  /* blocks; 0 = enough for n */
+    uint32_t reserved;
+} gx_launch;
+
+/*
+ * Run the program once per event over n records at events_dev (n * ctx_size bytes,
+ * 16-byte aligned), one event per thread, asynchronously on `stream`.  Maps keep their
+ * state across runs.  Ring-buffer records get event_idx = index within this call.
+ */
+int gx_run_batch(gx_prog *prog, const void *events_dev, uint64_t n, void *stream);
+/*
+ * As gx_run_batch, plus: event_idx_base is added to ring-buffer event indices;
+ * ret_out_dev (nullable) receives R0 of every event as int64; lp (nullable) fixes the
+ * launch shape instead of the tuned one.
+ */
+int gx_run_batch_ex(gx_prog *prog, const void *events_dev, uint64_t n, uint64_t event_idx_base,
+                    int64_t *ret_out_dev, const gx_launch *lp, void *stream);
+/*
+ * End-to-end form for host-resident events: copies events_host (pinned or pageable) to
+ * the device in chunks on two internal streams overlapping copy and execution, runs the
+ * program, and copies R0 back to ret_out_host (nullable).  Synchronous.
+ */
+int gx_run_batch_host(gx_prog *prog, const void *events_host, uint64_t n, int64_t *ret_out_host);
+
+typedef struct gx_run_stats {
+    int32_t status;         /* first device error (GX_E_BUDGET, GX_E_TIMEOUT, GX_E_DEVICE) or 0 */
+    uint32_t reserved;
+    uint64_t budget_trips;  /* events stopped by the instruction budget */
+    uint64_t waits_expired; /* bounded device waits that gave up */
+    uint64_t launches;      /* kernel launches issued for this program */
+} gx_run_stats;
+/* Synchronise `stream`, then report (and if reset != 0, clear) the program's status. */
+int gx_last_status(gx_prog *prog, gx_run_stats *out, int reset, void *stream);
+
+/*
+ * Pick block size and events per thread for (prog, n) by timing candidate shapes on a
+ * scratch copy of the program's maps (the real maps are not touched).  The choice is
+ * cached per program and size bucket and used by later runs; *best (nullable) gets it.
+ */
+int gx_autotune(gx_prog *prog, const void *events_dev, uint64_t n, void *stream, gx_launch *best);
+
+/* ---------------------------------------------------------------- batched form (Sec. 4.3.2, Sec. 5.3) */
+/*
+ * A batch is a fixed set of (program, events, n) items run by ONE persistent kernel:
+ * blocks claim chunks of events from an atomic cursor, switch programs by restaging the
+ * decoded program into shared memory, and the whole launch (cursor reset + kernel) is
+ * captured once into a CUDA graph.
+ */
+int gx_batch_create(gx_ctx *ctx, gx_batch **out);
+/* Add an item; ret_out_dev nullable.  Items may share programs and maps. */
+int gx_batch_add(gx_batch *b, gx_prog *prog, const void *events_dev, uint64_t n, int64_t *ret_out_dev);
+/* Build the chunk table and capture the graph; lp (nullable) fixes block/ept (else autotuned). */
+int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream);
+/* Launch the captured graph on `stream` (async). */
+int gx_batch_launch(gx_batch *b, void *stream);
+int gx_batch_destroy(gx_batch *b);
+
+/* ---------------------------------------------------------------- served form */
+typedef struct gx_server_opts {
+    uint64_t mem_budget;   /* admission budget: resident map bytes + in-flight event bytes (0 = none) */
+    uint32_t max_inflight; /* launches in flight, each on its own stream, 1..8 */
+    uint32_t max_items;    /* requests per tick, 1..4096 */
+    uint32_t block;        /* persistent kernel block size, 64..256 (0 = 256) */
+    uint32_t ept;          /* events per thread per chunk (0 = 4) */
+    uint32_t plain;        /* 1: no batching, one gx_run_batch launch per request (the baseline) */
+    uint32_t reserved;
+} gx_server_opts;
+
+typedef struct gx_completion {
+    uint64_t tag;         /* caller's tag from gx_server_submit */
+    int32_t status;       /* 0 or a GX_E* code */
+    uint32_t reserved;
+    double t_arrival;     /* seconds, steady clock: the request's (scheduled) arrival */
+    double t_start;       /* when the launch that ran it was issued */
+    double t_done;        /* when that launch was seen complete */
+} gx_completion;
+
+/*
+ * Continuous-batching server over one device.  A host thread admits submitted requests
+ * while (resident map bytes + event bytes of admitted, unfinished requests) stays within
+ * mem_budget, packs admitted requests into the next tick's chunk table, and launches the
+ * tick's captured graph (cursor reset + persistent kernel) on one of max_inflight
+ * streams, so ticks overlap on the device.  Requests that arrive while ticks run join the
+ * next tick as soon as a stream and memory are free.  Map state stays resident across
+ * requests.  With opts.plain = 1 the same loop issues one plain launch per request
+ * instead, which is the baseline the batched form is compared with.
+ * submit/poll may be called from one host thread concurrently with the server thread.
+ */
+int gx_server_create(gx_ctx *ctx, const gx_server_opts *opts, gx_server **out);
+/*
+ * Enqueue a request (non-blocking).  t_arrival: its arrival time on the gx_now() clock
+ * used for latency (0 = now).  GX_E_ADMISSION if it alone exceeds the budget.
+ */
+int gx_server_submit(gx_server *s, gx_prog *prog, const void *events_dev, uint64_t n, int64_t *ret_out_dev,
+                     uint64_t tag, double t_arrival);
+
+typedef struct gx_request {
+    gx_prog *prog;
+    const void *events_dev;
+    uint64_t n;
+    int64_t *ret_out_dev; /* nullable */
+    uint64_t tag;
+    double t_offset; /* seconds after the replay start */
+} gx_request;
+/*
+ * Open-loop load generator: submit reqs[i] at t0 + reqs[i].t_offset (busy-waiting on the
+ * calling thread), with that time as its arrival.  t0 = 0 means now.  Returns once every
+ * request has been submitted; collect results with gx_server_poll.
+ */
+int gx_server_replay(gx_server *s, const gx_request *reqs, uint32_t n, double t0);
+/* Collect up to cap completions; waits up to wait_ms for at least one (0 = no wait). */
+int gx_server_poll(gx_server *s, gx_completion *out, uint32_t cap, uint32_t *n_out, int wait_ms);
+/* Stop after finishing admitted work; frees the server. */
+int gx_server_destroy(gx_server *s);
+/* Steady-clock seconds, the time base of gx_completion. */
+double gx_now(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GX_H */

@@ -1,0 +1,10 @@
+"""gx: a device-side eBPF execution engine for GB300 (sm_103a).
+
+The native library (verifier, decoder, CUDA kernels, runtime) is built in-tree by
+`_build.build()` and bound by `gx.py`; see include/gx.h for the C ABI.
+"""
+from .gx import (  # noqa: F401
+    ANY, E_ADMISSION, E_BUDGET, E_CUDA, E_DEVICE, E_NODEV, E_TIMEOUT, E_VERIFY, E2BIG, EAGAIN, EEXIST, EINVAL,
+    ENOENT, ENOMEM, EXIST, MAP_ARRAY, MAP_HASH, MAP_RINGBUF, NOEXIST, Batch, Context, GxError, Map, Program, Server,
+    check, exported_symbols, lib, now, parse_records, verify,
+)

@@ -1,0 +1,353 @@
+"""Thin ctypes binding of the C ABI in include/gx.h (argument marshalling only).
+
+Every step of the execution path runs in the native library `_build/libgx.so`: the
+verifier, the decoder and the CUDA kernels.  Importing this module fails loudly when the
+library is missing; there is no fallback implementation.
+
+Device buffers are passed as torch CUDA tensors (their data_ptr) or raw integer
+addresses; streams as torch.cuda.Stream or None (legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _build
+
+OK = 0
+ENOENT, E2BIG, EAGAIN, ENOMEM, EFAULT, EEXIST, EINVAL, ENOSPC = -2, -7, -11, -12, -14, -17, -22, -28
+E_VERIFY, E_CUDA, E_BUDGET, E_TIMEOUT, E_DEVICE, E_ADMISSION, E_NODEV = -1000, -1001, -1002, -1003, -1004, -1005, -1006
+MAP_HASH, MAP_ARRAY, MAP_RINGBUF = 1, 2, 27
+ANY, NOEXIST, EXIST = 0, 1, 2
+
+u8p = ctypes.c_void_p
+u32, u64, i32, i64, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+
+
+class MapSpec(ctypes.Structure):
+    _fields_ = [("type", u32), ("key_size", u32), ("value_size", u32), ("max_entries", u32)]
+
+
+class ProgOpts(ctypes.Structure):
+    _fields_ = [("ctx_size", u32), ("deterministic", u32), ("insn_budget", u64), ("flags", u32), ("reserved", u32)]
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("block", u32), ("ept", u32), ("grid", u32), ("reserved", u32)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("status", i32), ("reserved", u32), ("budget_trips", u64), ("waits_expired", u64),
+                ("launches", u64)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget", u64), ("max_inflight", u32), ("max_items", u32), ("block", u32), ("ept", u32),
+                ("plain", u32), ("reserved", u32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", u64), ("status", i32), ("reserved", u32), ("t_arrival", dbl), ("t_start", dbl),
+                ("t_done", dbl)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("prog", ctypes.c_void_p), ("events_dev", ctypes.c_void_p), ("n", u64), ("ret_out_dev", ctypes.c_void_p),
+                ("tag", u64), ("t_offset", dbl)]
+
+
+_SIGS = {
+    "gx_init": (i32, [i32, u64, ctypes.POINTER(ctypes.c_void_p)]),
+    "gx_shutdown": (i32, [ctypes.c_void_p]),
+    "gx_mem_used": (u64, [ctypes.c_void_p]),
+    "gx_strerror": (ctypes.c_char_p, [i32]),
+    "gx_map_create": (i32, [ctypes.c_void_p, u32, u32, u32, u32, u32, ctypes.POINTER(ctypes.c_void_p)]),
+    "gx_map_destroy": (i32, [ctypes.c_void_p]),
+    "gx_map_bytes": (u64, [ctypes.c_void_p]),
+    "gx_map_read": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(u64), ctypes.c_void_p]),
+    "gx_map_write": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p]),
+    "gx_map_clear": (i32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gx_ringbuf_drain": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                               ctypes.c_void_p]),
+    "gx_verify": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                        ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
+                             ctypes.POINTER(ProgOpts), ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
+                             ctypes.c_size_t]),
+    "gx_prog_destroy": (i32, [ctypes.c_void_p]),
+    "gx_prog_uops": (u32, [ctypes.c_void_p]),
+    "gx_run_batch": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p]),
+    "gx_run_batch_ex": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, u64, ctypes.c_void_p, ctypes.POINTER(Launch),
+                              ctypes.c_void_p]),
+    "gx_run_batch_host": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p]),
+    "gx_last_status": (i32, [ctypes.c_void_p, ctypes.POINTER(RunStats), i32, ctypes.c_void_p]),
+    "gx_autotune": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p, ctypes.POINTER(Launch)]),
+    "gx_batch_create": (i32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "gx_batch_add": (i32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p]),
+    "gx_batch_plan": (i32, [ctypes.c_void_p, ctypes.POINTER(Launch), ctypes.c_void_p]),
+    "gx_batch_launch": (i32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gx_batch_destroy": (i32, [ctypes.c_void_p]),
+    "gx_server_create": (i32, [ctypes.c_void_p, ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    "gx_server_submit": (i32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p, u64, dbl]),
+    "gx_server_replay": (i32, [ctypes.c_void_p, ctypes.POINTER(Request), u32, dbl]),
+    "gx_server_poll": (i32, [ctypes.c_void_p, ctypes.POINTER(Completion), u32, ctypes.POINTER(u32), i32]),
+    "gx_server_destroy": (i32, [ctypes.c_void_p]),
+    "gx_now": (dbl, []),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the native library (building it first if it is absent or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    return list(_SIGS)
+
+
+class GxError(RuntimeError):
+    def __init__(self, status: int, what: str = "", log: str = "") -> None:
+        msg = lib().gx_strerror(status).decode()
+        super().__init__(f"{what}: {msg} ({status})" + (f": {log}" if log else ""))
+        self.status = status
+        self.log = log
+
+
+def check(rc: int, what: str = "") -> int:
+    if rc != 0:
+        raise GxError(rc, what)
+    return rc
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def now() -> float:
+    return lib().gx_now()
+
+
+def verify(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, deterministic: bool = False,
+           insn_budget: int = 0) -> Tuple[int, str]:
+    """Host-only verification: (status, log)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    specs = (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"])
+                                                   for s in map_specs])
+    opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
+    log = ctypes.create_string_buffer(1024)
+    rc = lib().gx_verify(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), log, 1024)
+    return rc, log.value.decode()
+
+
+class Context:
+    def __init__(self, device: int = 0, mem_budget: int = 0) -> None:
+        h = ctypes.c_void_p()
+        check(lib().gx_init(device, mem_budget, ctypes.byref(h)), "gx_init")
+        self.h = h
+
+    def mem_used(self) -> int:
+        return lib().gx_mem_used(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            check(lib().gx_shutdown(self.h), "gx_shutdown")
+            self.h = None
+
+
+class Map:
+    def __init__(self, ctx: Context, type: int, key_size: int, value_size: int, max_entries: int) -> None:
+        h = ctypes.c_void_p()
+        check(lib().gx_map_create(ctx.h, type, key_size, value_size, max_entries, 0, ctypes.byref(h)), "gx_map_create")
+        self.h, self.ctx = h, ctx
+        self.type, self.key_size, self.value_size, self.max_entries = type, key_size, value_size, max_entries
+
+    @classmethod
+    def from_spec(cls, ctx: Context, spec: dict) -> "Map":
+        return cls(ctx, spec["type"], spec["key_size"], spec["value_size"], spec["max_entries"])
+
+    def destroy(self) -> None:
+        if self.h:
+            check(lib().gx_map_destroy(self.h), "gx_map_destroy")
+            self.h = None
+
+    def nbytes(self) -> int:
+        return lib().gx_map_bytes(self.h)
+
+    def read_raw(self, stream=None) -> Tuple[bytes, int]:
+        if self.type == MAP_ARRAY:
+            cap = self.max_entries * self.value_size
+        else:
+            cap = self.max_entries * (self.key_size + self.value_size)
+        buf = np.zeros(max(cap, 1), dtype=np.uint8)
+        n = u64(0)
+        check(lib().gx_map_read(self.h, buf.ctypes.data, cap, ctypes.byref(n), _stream(stream)), "gx_map_read")
+        used = self.max_entries * self.value_size if self.type == MAP_ARRAY else n.value * (self.key_size + self.value_size)
+        return buf[:used].tobytes(), n.value
+
+    def array_values(self, stream=None) -> np.ndarray:
+        raw, _ = self.read_raw(stream)
+        return np.frombuffer(raw, dtype=np.uint8).reshape(self.max_entries, self.value_size)
+
+    def array_u64(self, stream=None) -> np.ndarray:
+        return self.array_values(stream).view("<u8").reshape(self.max_entries, self.value_size // 8)
+
+    def hash_items(self, stream=None) -> Dict[bytes, bytes]:
+        raw, n = self.read_raw(stream)
+        st = self.key_size + self.value_size
+        return {raw[i * st:i * st + self.key_size]: raw[i * st + self.key_size:(i + 1) * st] for i in range(n)}
+
+    def write(self, data: bytes, stream=None) -> None:
+        buf = np.frombuffer(data, dtype=np.uint8).copy()
+        check(lib().gx_map_write(self.h, buf.ctypes.data, buf.size, _stream(stream)), "gx_map_write")
+
+    def clear(self, stream=None) -> None:
+        check(lib().gx_map_clear(self.h, _stream(stream)), "gx_map_clear")
+
+    def drain(self, stream=None) -> Tuple[bytes, int]:
+        """Ring buffer: (packed committed records, drops since the last drain)."""
+        buf = np.zeros(self.max_entries, dtype=np.uint8)
+        nb, dropped = u64(0), u64(0)
+        check(lib().gx_ringbuf_drain(self.h, buf.ctypes.data, buf.size, ctypes.byref(nb), ctypes.byref(dropped),
+                                     _stream(stream)), "gx_ringbuf_drain")
+        return buf[:nb.value].tobytes(), dropped.value
+
+
+class Program:
+    def __init__(self, ctx: Context, insns: np.ndarray, maps: Sequence[Map], ctx_size: int,
+                 deterministic: bool = False, insn_budget: int = 0) -> None:
+        insns = np.ascontiguousarray(insns, dtype=np.uint64)
+        arr = (ctypes.c_void_p * max(1, len(maps)))(*[m.h for m in maps])
+        opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
+        log = ctypes.create_string_buffer(1024)
+        h = ctypes.c_void_p()
+        rc = lib().gx_verify_load(ctx.h, insns.ctypes.data, insns.size, arr, len(maps), ctypes.byref(opts),
+                                  ctypes.byref(h), log, 1024)
+        if rc:
+            raise GxError(rc, "gx_verify_load", log.value.decode())
+        self.h, self.ctx, self.maps, self.ctx_size = h, ctx, list(maps), ctx_size
+
+    def destroy(self) -> None:
+        if self.h:
+            check(lib().gx_prog_destroy(self.h), "gx_prog_destroy")
+            self.h = None
+
+    def uops(self) -> int:
+        return lib().gx_prog_uops(self.h)
+
+    def run(self, events, n: Optional[int] = None, *, ret_out=None, idx_base: int = 0,
+            launch: Optional[Tuple[int, int]] = None, stream=None) -> None:
+        if n is None:
+            n = events.numel() * events.element_size() // self.ctx_size
+        lp = None if launch is None else ctypes.byref(Launch(launch[0], launch[1], 0, 0))
+        check(lib().gx_run_batch_ex(self.h, _ptr(events), n, idx_base, _ptr(ret_out), lp, _stream(stream)),
+              "gx_run_batch_ex")
+
+    def run_host(self, events_host: np.ndarray, ret_out_host: Optional[np.ndarray] = None) -> None:
+        raw = events_host.view(np.uint8).reshape(-1)
+        n = raw.size // self.ctx_size
+        check(lib().gx_run_batch_host(self.h, raw.ctypes.data, n, _ptr(ret_out_host)), "gx_run_batch_host")
+
+    def status(self, reset: bool = False, stream=None) -> RunStats:
+        st = RunStats()
+        check(lib().gx_last_status(self.h, ctypes.byref(st), int(reset), _stream(stream)), "gx_last_status")
+        return st
+
+    def autotune(self, events, n: Optional[int] = None, stream=None) -> Tuple[int, int]:
+        if n is None:
+            n = events.numel() * events.element_size() // self.ctx_size
+        best = Launch()
+        check(lib().gx_autotune(self.h, _ptr(events), n, _stream(stream), ctypes.byref(best)), "gx_autotune")
+        return best.block, best.ept
+
+
+class Batch:
+    def __init__(self, ctx: Context) -> None:
+        h = ctypes.c_void_p()
+        check(lib().gx_batch_create(ctx.h, ctypes.byref(h)), "gx_batch_create")
+        self.h = h
+
+    def add(self, prog: Program, events, n: int, ret_out=None) -> None:
+        check(lib().gx_batch_add(self.h, prog.h, _ptr(events), n, _ptr(ret_out)), "gx_batch_add")
+
+    def plan(self, launch: Optional[Tuple[int, int]] = None, stream=None) -> None:
+        lp = None if launch is None else ctypes.byref(Launch(launch[0], launch[1], 0, 0))
+        check(lib().gx_batch_plan(self.h, lp, _stream(stream)), "gx_batch_plan")
+
+    def launch(self, stream=None) -> None:
+        check(lib().gx_batch_launch(self.h, _stream(stream)), "gx_batch_launch")
+
+    def destroy(self) -> None:
+        if self.h:
+            check(lib().gx_batch_destroy(self.h), "gx_batch_destroy")
+            self.h = None
+
+
+class Server:
+    def __init__(self, ctx: Context, mem_budget: int = 0, max_inflight: int = 2, max_items: int = 1024,
+                 block: int = 256, ept: int = 4, plain: bool = False) -> None:
+        opts = ServerOpts(mem_budget, max_inflight, max_items, block, ept, int(plain), 0)
+        h = ctypes.c_void_p()
+        check(lib().gx_server_create(ctx.h, ctypes.byref(opts), ctypes.byref(h)), "gx_server_create")
+        self.h = h
+
+    def submit(self, prog: Program, events, n: int, ret_out=None, tag: int = 0, t_arrival: float = 0.0) -> None:
+        check(lib().gx_server_submit(self.h, prog.h, _ptr(events), n, _ptr(ret_out), tag, t_arrival),
+              "gx_server_submit")
+
+    def replay(self, reqs: Sequence[Tuple[Program, object, int, object, int, float]], t0: float = 0.0) -> None:
+        arr = (Request * len(reqs))()
+        for i, (p, ev, n, ro, tag, toff) in enumerate(reqs):
+            arr[i] = Request(p.h, _ptr(ev), n, _ptr(ro), tag, toff)
+        check(lib().gx_server_replay(self.h, arr, len(reqs), t0), "gx_server_replay")
+
+    def poll(self, cap: int = 4096, wait_ms: int = 0) -> List[Completion]:
+        buf = (Completion * cap)()
+        n = u32(0)
+        check(lib().gx_server_poll(self.h, buf, cap, ctypes.byref(n), wait_ms), "gx_server_poll")
+        return [buf[i] for i in range(n.value)]
+
+    def destroy(self) -> None:
+        if self.h:
+            check(lib().gx_server_destroy(self.h), "gx_server_destroy")
+            self.h = None
+
+
+def parse_records(raw: bytes) -> List[Tuple[int, bytes]]:
+    """Split a drained record stream into (event_idx, payload) in stream order."""
+    out, pos = [], 0
+    while pos + 16 <= len(raw):
+        ln = int.from_bytes(raw[pos:pos + 4], "little")
+        idx = int.from_bytes(raw[pos + 8:pos + 16], "little")
+        out.append((idx, raw[pos + 16:pos + 16 + ln]))
+        pos += 16 + ((ln + 7) & ~7)
+    return out

@@ -310,6 +310,9 @@ def random_program(seed: int, target_len: int, use_hash: bool = True) -> Tuple[n
     rng = _Rng(seed)
     a = Asm()
     lbl = [0]
+    # one update operation per map keeps every result independent of event order:
+    # add, or, xor and max each commute with themselves but not with one another
+    arr_op = rng.choice(["add", "or", "xor", "max"])
 
     def fresh() -> str:
         lbl[0] += 1
@@ -333,8 +336,11 @@ def random_program(seed: int, target_len: int, use_hash: bool = True) -> Tuple[n
             width = rng.choice([16, 32, 64])
             order = rng.choice(["le", "be", "swap"])
             a.end(dst, width, order)
-        elif op in ("lsh", "rsh", "arsh") and rng.below(2) == 0:
-            a.alu(op, dst, rng.below(bits), bits=bits)
+        elif op in ("lsh", "rsh", "arsh"):
+            if rng.below(2) == 0:
+                a.alu(op, dst, rng.below(bits), bits=bits)  # constant shifts stay below the width
+            else:
+                a.alu(op, dst, rng.choice(regs), bits=bits)
         elif rng.below(2) == 0:
             imm = rng.choice([1, 3, 7, 255, -1, 0x7FFF, -12345, 1 << 20, rng.below(1 << 31)])
             if op in ("div", "mod") and rng.below(4) == 0:
@@ -347,6 +353,9 @@ def random_program(seed: int, target_len: int, use_hash: bool = True) -> Tuple[n
     while len(a) < target_len - 3:
         kind = rng.below(10)
         regs = sorted(init)
+        if target_len - 3 - len(a) < 32:  # near the end: single instructions only, never overshoot
+            alu_insn(regs)
+            continue
         if kind <= 3:
             for _ in range(1 + rng.below(5)):
                 alu_insn(regs)
@@ -384,7 +393,7 @@ def random_program(seed: int, target_len: int, use_hash: bool = True) -> Tuple[n
             end = fresh()
             a.jeq("r0", 0, end)
             val = rng.choice(["r7", "r8", "r9"])
-            op = rng.choice(["add", "or", "xor", "max", "add"])
+            op = arr_op
             if op == "max":
                 a.mov("r1", "r0")
                 a.mov("r2", val)
