@@ -29,8 +29,20 @@
 #ifndef GX_H
 #define GX_H
 
+#ifdef __CUDACC_RTC__ /* compiled by NVRTC as part of a load-time specialised program */
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned long long uintptr_t;
+#else
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -83,6 +95,7 @@ extern "C" {
 #define GX_MAX_KEY 64
 #define GX_MAX_VALUE 4096
 
+#ifndef __CUDACC_RTC__ /* device code sees the constants above only */
 typedef struct gx_ctx gx_ctx;
 typedef struct gx_map gx_map;
 typedef struct gx_prog gx_prog;
@@ -162,9 +175,25 @@ typedef struct gx_prog_opts {
     uint32_t ctx_size;      /* bytes of one event record: multiple of 8 in [8, GX_MAX_CTX] */
     uint32_t deterministic; /* 1: also reject programs whose results could depend on event order */
     uint64_t insn_budget;   /* per-event limit on taken backward jumps; 0 = 1<<16 */
-    uint32_t flags;         /* reserved, 0 */
+    uint32_t flags;         /* GX_PROG_* bits */
     uint32_t reserved;
 } gx_prog_opts;
+
+/*
+ * opts.flags: GX_PROG_JIT runs the program as load-time specialised device code (one
+ * CUDA function generated from the verified bytecode, compiled by NVRTC for sm_103a)
+ * instead of through the interpreter kernel.  Results are identical; gx_verify_load
+ * returns GX_E_NODEV if the runtime compiler is unavailable.
+ */
+#define GX_PROG_JIT 1u
+
+/*
+ * Host only: verify a program and compile its specialised form to sm_103a code without
+ * loading it (no device needed; NVRTC must be available).  0, GX_E_VERIFY, GX_E_NODEV
+ * (no runtime compiler) or GX_E_CUDA (compile error); `log` explains.
+ */
+int gx_jit_check(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+                 const gx_prog_opts *opts, char *log, size_t log_len);
 
 /*
  * Verify `n_insns` raw eBPF slots (RFC 9669 encoding, little-endian) against map specs,
@@ -301,6 +330,7 @@ int gx_server_poll(gx_server *s, gx_completion *out, uint32_t cap, uint32_t *n_o
 int gx_server_destroy(gx_server *s);
 /* Steady-clock seconds, the time base of gx_completion. */
 double gx_now(void);
+#endif /* !__CUDACC_RTC__ */
 
 #ifdef __cplusplus
 }

@@ -26,9 +26,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + os.path.join(CUDA_HOME, "include")]
 
-CU_SOURCES = ["engine.cu"]
-CXX_SOURCES = ["verifier.cpp", "decode.cpp", "api.cpp", "batch.cpp"]
-HEADERS = ["gx_layout.h", "gx_internal.h", "gx_kernels.h", "gx_runtime.h"]
+CU_SOURCES = ["interp.cu"]
+CXX_SOURCES = ["verifier.cpp", "decode.cpp", "api.cpp", "batch.cpp", "jit.cpp"]
+HEADERS = ["gx_layout.h", "gx_internal.h", "gx_kernels.h", "gx_runtime.h", "gx_device.cuh", "gx_jit.h"]
 
 
 def _stamp() -> str:
@@ -73,6 +73,26 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+EMBED = [("gx_h", os.path.join(INCLUDE, "gx.h")), ("gx_layout_h", os.path.join(CSRC, "gx_layout.h")),
+         ("gx_device_cuh", os.path.join(CSRC, "gx_device.cuh"))]
+
+
+def _write_embed() -> str:
+    """The device headers as C strings, handed to NVRTC when programs are specialised."""
+    out = os.path.join(BUILD, "gx_embed.cpp")
+    parts = ["/* generated by _build.py: device headers for load-time compilation */\n"]
+    for name, path in EMBED:
+        with open(path) as fh:
+            text = fh.read()
+        assert ")GXEMBED\"" not in text
+        parts.append(f'extern "C" const char gx_embed_{name}[] = R"GXEMBED({text})GXEMBED";\n')
+    body = "".join(parts)
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as fh:
+            fh.write(body)
+    return out
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libgx.so if the sources changed; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
@@ -85,11 +105,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if shutil.which(NVCC) is None and not os.path.exists(NVCC):
         raise RuntimeError(f"nvcc not found at {NVCC}")
     srcs = CU_SOURCES + CXX_SOURCES
-    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+    embed = _write_embed()
+    with ThreadPoolExecutor(max_workers=len(srcs) + 1) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        embed_obj = os.path.join(BUILD, "gx_embed.o")
+        r = subprocess.run(["g++", "-c", "-fPIC", "-O1", embed, "-o", embed_obj], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"embed compile failed\n{r.stderr}")
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-shared", "-o", tmp] + objs + ["-L" + os.path.join(CUDA_HOME, "lib64"), "-lcudart", "-lpthread",
-                                                  "-Wl,-rpath," + os.path.join(CUDA_HOME, "lib64")]
+    cmd = ["g++", "-shared", "-o", tmp] + objs + [embed_obj, "-L" + os.path.join(CUDA_HOME, "lib64"), "-lcudart",
+                                                  "-lpthread", "-ldl", "-Wl,-rpath," + os.path.join(CUDA_HOME, "lib64")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

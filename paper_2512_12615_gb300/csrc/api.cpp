@@ -125,7 +125,12 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     P.n = n;
     P.idx_base = idx_base;
     P.ret_out = (long long *)ret_out;
-    rc = cuda_status(launch_exec(P, (unsigned)grid, block, smem, s));
+    if (p->jit) {
+        rc = cuda_status(jit_set_smem(p->jk, smem));
+        if (rc == GX_OK) rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s));
+    } else {
+        rc = cuda_status(launch_exec(P, (unsigned)grid, block, smem, s));
+    }
     if (rc == GX_OK) p->launches++;
     return rc;
 }
@@ -428,6 +433,7 @@ int gx_verify(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32
 int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len) {
     if (!c || !insns || !opts || !out || (n_maps && !maps)) return GX_EINVAL;
+    if (opts->flags & ~GX_PROG_JIT) return GX_EINVAL;
     *out = nullptr;
     std::vector<gx_map_spec> specs(n_maps);
     for (uint32_t i = 0; i < n_maps; i++) {
@@ -444,6 +450,15 @@ int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *
         p->ctx = c;
         p->opts = *opts;
         rc = decode_program(insns, n, v, p->uops, msg);
+        if (rc == GX_OK) {
+            p->jp.insns.assign(insns, insns + n);
+            p->jp.info = v.info;
+            p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+            if (opts->flags & GX_PROG_JIT) {
+                rc = jit_build({&p->jp}, p->jk, msg);
+                p->jit = rc == GX_OK;
+            }
+        }
     }
     if (log && log_len) {
         size_t k = std::min(log_len - 1, msg.size());

@@ -19,6 +19,7 @@ struct InsnInfo {
     uint8_t visited = 0;
     uint8_t kind = MK_NONE; /* region of a load / store / atomic */
     int16_t off = 0;        /* MK_CTX: absolute ctx offset; MK_STACK: offset from the frame top */
+    int8_t map = -1;        /* helper call: map index in R1 on every path, -2 if it varies */
 };
 
 struct VerifyOut {

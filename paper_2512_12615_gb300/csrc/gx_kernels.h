@@ -9,22 +9,7 @@
 
 namespace gx {
 
-struct ExecParams {
-    const uint8_t *image;  /* plain mode: the program image */
-    uint32_t image_bytes;  /* plain mode: its size (multiple of 16) */
-    uint32_t image_area;   /* shared-memory bytes reserved for images; ctx tiles follow */
-    uint32_t ctx_size;     /* plain mode: bytes per record */
-    uint32_t ept;          /* plain mode: tiles of blockDim events per block */
-    uint32_t mode;         /* 0 = plain, 1 = persistent chunk table */
-    uint32_t nchunks;
-    const uint8_t *events; /* plain mode */
-    uint64_t n;
-    uint64_t idx_base;
-    long long *ret_out;
-    const gx_chunk *chunks; /* persistent mode */
-    unsigned int *cursor;   /* persistent mode: next chunk to claim */
-    const unsigned int *nchunks_dev; /* persistent mode: if set, the chunk count is read here */
-};
+typedef gx_exec_params ExecParams;
 
 cudaError_t exec_set_smem(size_t bytes);
 cudaError_t exec_occupancy(int block, size_t smem, int *blocks_per_sm);

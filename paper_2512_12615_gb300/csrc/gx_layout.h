@@ -19,7 +19,9 @@
 #ifndef GX_LAYOUT_H
 #define GX_LAYOUT_H
 
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
+#endif
 
 /*
  * Register-specialised families: the handler id carries the eBPF register (16 slots per
@@ -66,9 +68,11 @@ enum gx_family { GX_FAMILIES(GX_ENUM_FAM) GX_NUM_FAMILIES };
 enum gx_single { GX_SINGLES(GX_ENUM_SINGLE) GX_NUM_SINGLES };
 #define GX_NUM_HANDLERS (GX_SINGLE_BASE + GX_NUM_SINGLES)
 
+#ifndef __CUDACC_RTC__
 static inline uint64_t gx_uop(uint32_t handler, uint32_t aux, int32_t imm) {
     return (uint64_t)(handler & 0xFFFFu) | ((uint64_t)(aux & 0xFFFFu) << 16) | ((uint64_t)(uint32_t)imm << 32);
 }
+#endif
 
 /* ---------------------------------------------------------------- device map descriptor */
 #define GX_SLOT_EMPTY 0u
@@ -120,6 +124,24 @@ typedef struct gx_chunk {
     uint32_t ctx_size;
     uint64_t pad;
 } gx_chunk;
+
+/* kernel parameters of the interpreter and of specialised programs */
+typedef struct gx_exec_params {
+    const uint8_t *image;  /* plain mode: the program image */
+    uint32_t image_bytes;  /* plain mode: its size (multiple of 16) */
+    uint32_t image_area;   /* shared-memory bytes reserved for images; ctx tiles follow */
+    uint32_t ctx_size;     /* plain mode: bytes per record */
+    uint32_t ept;          /* plain mode: tiles of blockDim events per block */
+    uint32_t mode;         /* 0 = plain, 1 = persistent chunk table */
+    uint32_t nchunks;
+    const uint8_t *events; /* plain mode */
+    uint64_t n;
+    uint64_t idx_base;
+    long long *ret_out;
+    const gx_chunk *chunks; /* persistent mode */
+    unsigned int *cursor;   /* persistent mode: next chunk to claim */
+    const unsigned int *nchunks_dev; /* persistent mode: if set, the chunk count is read here */
+} gx_exec_params;
 
 #ifdef __cplusplus
 static_assert(sizeof(gx_dmap) == 64, "descriptor size");

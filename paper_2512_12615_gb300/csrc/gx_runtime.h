@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "gx_internal.h"
+#include "gx_jit.h"
 
 #define GX_MAX_BLOCK 256                   /* the exec kernel's launch bound */
 #define GX_MAX_IMAGE (160u * 1024u)        /* decoded image must fit in shared memory */
@@ -53,6 +54,10 @@ struct gx_prog {
     unsigned long long *dstats = nullptr;
     uint64_t launches = 0;
     std::map<int, gx_launch> tuned; /* log2(n) bucket -> shape */
+    /* load-time specialisation (GX_PROG_JIT) */
+    gx::JitProgram jp;
+    gx::JitKernel jk;
+    bool jit = false;
     /* gx_run_batch_host staging */
     void *stage[2] = {nullptr, nullptr};
     uint64_t stage_bytes = 0;

@@ -1,0 +1,505 @@
+/*
+ * Load-time specialisation of verified programs (the paper's eBPF -> device-code JIT
+ * with helper inlining, Sec. 4.4.2 and Sec. 5.3).
+ *
+ * Each verified program becomes one straight-line CUDA C++ function: eBPF registers are
+ * local variables, every instruction is one C statement, jumps are gotos, ctx and stack
+ * accesses use the offsets the verifier proved, helper calls name their map directly.
+ * The function is wrapped into the same launch skeleton as the interpreter
+ * (gx_device.cuh: exec_tiles), compiled by NVRTC for sm_103a and loaded with the CUDA
+ * runtime's library API.  A kernel may hold several programs (a batch): it switches on
+ * the chunk's program slot.  NVRTC is loaded with dlopen, so the engine library keeps
+ * loading on hosts without the compiler or a GPU; compiled cubins are cached in memory
+ * and, if GX_JIT_CACHE names a directory, on disk.
+ */
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <stdio.h>
+#include <string.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "gx_jit.h"
+#include "gx_runtime.h"
+
+extern "C" const char gx_embed_gx_h[];
+extern "C" const char gx_embed_gx_layout_h[];
+extern "C" const char gx_embed_gx_device_cuh[];
+
+namespace gx {
+namespace {
+
+/* ---------------------------------------------------------------- NVRTC entry points */
+typedef int nvrtcResult_;
+typedef void *nvrtcProgram_;
+struct Nvrtc {
+    bool ok = false;
+    std::string err;
+    nvrtcResult_ (*create)(nvrtcProgram_ *, const char *, const char *, int, const char *const *,
+                           const char *const *) = nullptr;
+    nvrtcResult_ (*compile)(nvrtcProgram_, int, const char *const *) = nullptr;
+    nvrtcResult_ (*log_size)(nvrtcProgram_, size_t *) = nullptr;
+    nvrtcResult_ (*log)(nvrtcProgram_, char *) = nullptr;
+    nvrtcResult_ (*cubin_size)(nvrtcProgram_, size_t *) = nullptr;
+    nvrtcResult_ (*cubin)(nvrtcProgram_, char *) = nullptr;
+    nvrtcResult_ (*destroy)(nvrtcProgram_ *) = nullptr;
+};
+
+Nvrtc &nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"};
+        void *h = nullptr;
+        for (const char *nm : names)
+            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) {
+            n.err = "NVRTC library not found";
+            return;
+        }
+        n.create = (decltype(n.create))dlsym(h, "nvrtcCreateProgram");
+        n.compile = (decltype(n.compile))dlsym(h, "nvrtcCompileProgram");
+        n.log_size = (decltype(n.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+        n.log = (decltype(n.log))dlsym(h, "nvrtcGetProgramLog");
+        n.cubin_size = (decltype(n.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+        n.cubin = (decltype(n.cubin))dlsym(h, "nvrtcGetCUBIN");
+        n.destroy = (decltype(n.destroy))dlsym(h, "nvrtcDestroyProgram");
+        n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+        if (!n.ok) n.err = "NVRTC symbols missing";
+    });
+    return n;
+}
+
+/* ---------------------------------------------------------------- code generation */
+std::string hex64(uint64_t v) {
+    char b[32];
+    snprintf(b, sizeof b, "0x%llxull", (unsigned long long)v);
+    return b;
+}
+
+const char *alu_op(int code, int off) {
+    switch (code) {
+    case 0x00: return "O_ADD";
+    case 0x10: return "O_SUB";
+    case 0x20: return "O_MUL";
+    case 0x30: return off ? "O_SDIV" : "O_DIV";
+    case 0x40: return "O_OR";
+    case 0x50: return "O_AND";
+    case 0x60: return "O_LSH";
+    case 0x70: return "O_RSH";
+    case 0x90: return off ? "O_SMOD" : "O_MOD";
+    case 0xA0: return "O_XOR";
+    case 0xB0: return "O_MOV";
+    case 0xC0: return "O_ARSH";
+    }
+    return nullptr;
+}
+
+const char *cond_op(int code) {
+    switch (code) {
+    case 0x10: return "C_EQ";
+    case 0x20: return "C_GT";
+    case 0x30: return "C_GE";
+    case 0x40: return "C_SET";
+    case 0x50: return "C_NE";
+    case 0x60: return "C_SGT";
+    case 0x70: return "C_SGE";
+    case 0xA0: return "C_LT";
+    case 0xB0: return "C_LE";
+    case 0xC0: return "C_SLT";
+    case 0xD0: return "C_SLE";
+    }
+    return nullptr;
+}
+
+int size_of(int op) { return (op & 0x18) == 0x00 ? 4 : (op & 0x18) == 0x08 ? 2 : (op & 0x18) == 0x10 ? 1 : 8; }
+
+std::string R(int r) { return "r" + std::to_string(r); }
+
+/* one program -> `__device__ u64 gx_body_<slot>(env, ctxw, valid, ev_idx)` */
+int gen_body(const JitProgram &p, int slot, std::string &out, std::string &log) {
+    const uint32_t n = (uint32_t)p.insns.size();
+    std::vector<uint8_t> target(n + 1, 0);
+    for (uint32_t pc = 0; pc < n; pc++) {
+        if (!p.info[pc].visited) continue;
+        uint64_t w = p.insns[pc];
+        int op = (int)(w & 0xFF), cls = op & 7;
+        int off = (int)(int16_t)(uint16_t)((w >> 16) & 0xFFFF);
+        int32_t imm = (int32_t)(uint32_t)(w >> 32);
+        if (op == 0x18) {
+            pc++;
+            continue;
+        }
+        if ((cls == 5 || cls == 6) && ((op & 0xF0) != 0x80) && ((op & 0xF0) != 0x90)) {
+            int64_t t = (int64_t)pc + 1 + ((cls == 6 && (op & 0xF0) == 0) ? imm : off);
+            target[t] = 1;
+        }
+    }
+    std::ostringstream o;
+    o << "__device__ __forceinline__ u64 gx_body_" << slot
+      << "(const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {\n"
+      << "  if (!valid) return 0;\n"
+      << "  const u32 lane = threadIdx.x & 31;\n"
+      << "  u64 stack[" << GX_STACK_BYTES / 8 << "];\n"
+      << "  u64 r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0;\n"
+      << "  u64 r10 = (u64)(stack + " << GX_STACK_BYTES / 8 << ");\n"
+      << "  u64 back = 0;\n"
+      << "  (void)lane; (void)ev_idx; (void)back; (void)r10;\n";
+    const uint64_t budget = p.budget;
+    auto jump = [&](uint32_t pc, int64_t tgt) -> std::string {
+        std::string g = "goto L" + std::to_string(tgt) + ";";
+        if (tgt <= (int64_t)pc) return "{ if (++back > " + std::to_string(budget) + "ull) goto budget_trip; " + g + " }";
+        return g;
+    };
+    for (uint32_t pc = 0; pc < n; pc++) {
+        const InsnInfo &ii = p.info[pc];
+        uint64_t w = p.insns[pc];
+        int op = (int)(w & 0xFF), cls = op & 7;
+        int dst = (int)((w >> 8) & 0xF), src = (int)((w >> 12) & 0xF);
+        int off = (int)(int16_t)(uint16_t)((w >> 16) & 0xFFFF);
+        int32_t imm = (int32_t)(uint32_t)(w >> 32);
+        if (target[pc]) o << "L" << pc << ":;\n";
+        if (!ii.visited) {
+            if (op == 0x18) pc++;
+            continue;
+        }
+        o << "  ";
+        switch (cls) {
+        case 4: case 7: {
+            bool w32 = cls == 4, x = op & 8;
+            int code = op & 0xF0;
+            std::string d = R(dst);
+            if (code == 0xD0) {
+                if (w32 && !x) {
+                    if (imm == 16) o << d << " &= 0xFFFFull;";
+                    else if (imm == 32) o << d << " &= 0xFFFFFFFFull;";
+                    else o << ";";
+                } else if (imm == 16) {
+                    o << d << " = (u64)__byte_perm((u32)" << d << ", 0u, 0x4401u);";
+                } else if (imm == 32) {
+                    o << d << " = (u64)__byte_perm((u32)" << d << ", 0u, 0x0123u);";
+                } else {
+                    o << d << " = ((u64)__byte_perm((u32)" << d << ", 0u, 0x0123u) << 32) | (u64)__byte_perm((u32)("
+                      << d << " >> 32), 0u, 0x0123u);";
+                }
+                break;
+            }
+            if (code == 0x80) {
+                o << d << (w32 ? " = (u64)(u32)(0u - (u32)" + d + ");" : " = (u64)0 - " + d + ";");
+                break;
+            }
+            if (code == 0xB0 && off) {
+                const char *t = off == 8 ? "int8_t" : off == 16 ? "int16_t" : "int32_t";
+                if (w32) o << d << " = (u64)(u32)(int32_t)(" << t << ")" << R(src) << ";";
+                else o << d << " = (u64)(s64)(" << t << ")" << R(src) << ";";
+                break;
+            }
+            const char *oname = alu_op(code, off);
+            if (!oname) {
+                log = "jit: unknown ALU op";
+                return GX_EINVAL;
+            }
+            std::string s = x ? R(src) : (w32 ? hex64((uint32_t)imm) : hex64((uint64_t)(int64_t)imm));
+            if (code == 0xB0 && !w32) o << d << " = " << s << ";";
+            else o << d << " = " << (w32 ? "a32<" : "a64<") << oname << ">(" << d << ", " << s << ");";
+            break;
+        }
+        case 5: case 6: {
+            int code = op & 0xF0;
+            if (code == 0x00) {
+                int64_t t = (int64_t)pc + 1 + (cls == 6 ? imm : off);
+                o << jump(pc, t);
+                break;
+            }
+            if (code == 0x90) {
+                o << "return r0;";
+                break;
+            }
+            if (code == 0x80) {
+                std::string m = ii.map >= 0 ? "env.maps[" + std::to_string(ii.map) + "]" : "env.maps[r1]";
+                switch (imm) {
+                case GX_HELPER_MAP_LOOKUP:
+                    o << "r0 = map_lookup(" << m << ", (const uint8_t *)r2, __activemask(), env.stats);";
+                    break;
+                case GX_HELPER_MAP_UPDATE:
+                    o << "r0 = (u64)(s64)map_update(" << m
+                      << ", (const uint8_t *)r2, (const uint8_t *)r3, r4, __activemask(), env.stats);";
+                    break;
+                case GX_HELPER_MAP_DELETE:
+                    o << "r0 = (u64)(s64)(" << m << ".type == GX_MAP_HASH ? hash_delete(" << m
+                      << ", (const uint8_t *)r2, env.stats) : GX_EINVAL);";
+                    break;
+                case GX_HELPER_RINGBUF_RESERVE:
+                    o << "r0 = rb_reserve(" << m << ", r2, __activemask(), ev_idx);";
+                    break;
+                case GX_HELPER_RINGBUF_OUTPUT:
+                    o << "{ u64 p_ = rb_reserve(" << m << ", r3, __activemask(), ev_idx); if (p_) copy_bytes((uint8_t *)p_, "
+                      << "(const uint8_t *)r2, (u32)r3); r0 = p_ ? 0 : (u64)(s64)GX_EAGAIN; }";
+                    break;
+                case GX_HELPER_RINGBUF_SUBMIT:
+                    o << ";";
+                    break;
+                case GX_HELPER_RINGBUF_DISCARD:
+                    o << "((u32 *)(r1 - GX_RB_HDR))[1] = GX_RB_DISCARDED;";
+                    break;
+                case GX_HELPER_ATOMIC_MAX_U64:
+                    o << "agg_update<AG_MAX, 8>(r1, r2, __activemask());";
+                    break;
+                case GX_HELPER_ATOMIC_MIN_U64:
+                    o << "agg_update<AG_MIN, 8>(r1, r2, __activemask());";
+                    break;
+                default: log = "jit: unknown helper"; return GX_EINVAL;
+                }
+                break;
+            }
+            const char *c = cond_op(code);
+            if (!c) {
+                log = "jit: unknown jump";
+                return GX_EINVAL;
+            }
+            bool w32 = cls == 6, x = op & 8;
+            std::string s = x ? R(src) : (w32 ? hex64((uint32_t)imm) : hex64((uint64_t)(int64_t)imm));
+            int64_t t = (int64_t)pc + 1 + off;
+            o << "if (" << (w32 ? "c32<" : "c64<") << c << ">(" << R(dst) << ", " << s << ")) " << jump(pc, t);
+            break;
+        }
+        case 0: {
+            if (src == 1) o << R(dst) << " = " << imm << "ull;";
+            else o << R(dst) << " = " << hex64((uint64_t)(uint32_t)imm | ((p.insns[pc + 1] >> 32) << 32)) << ";";
+            pc++;
+            break;
+        }
+        case 1: {
+            int size = size_of(op);
+            bool sign = (op & 0xE0) == 0x80;
+            std::string ld = "load_sz<" + std::to_string(size) + ", " + (sign ? "true" : "false") + ">(";
+            if (ii.kind == MK_CTX)
+                o << R(dst) << " = " << ld << "(const uint8_t *)(ctxw + " << ((ii.off >> 3) << 5) << " + lane) + "
+                  << (ii.off & 7) << ");";
+            else if (ii.kind == MK_STACK)
+                o << R(dst) << " = " << ld << "(const uint8_t *)stack + " << ii.off + GX_STACK_BYTES << ");";
+            else
+                o << R(dst) << " = " << ld << "(const uint8_t *)(" << R(src) << " + " << hex64((uint64_t)(int64_t)off)
+                  << "));";
+            break;
+        }
+        case 2: case 3: {
+            int size = size_of(op);
+            std::string addr = ii.kind == MK_STACK
+                                   ? "(u64)((uint8_t *)stack + " + std::to_string(ii.off + GX_STACK_BYTES) + ")"
+                                   : "(" + R(dst) + " + " + hex64((uint64_t)(int64_t)off) + ")";
+            if ((op & 0xE0) == 0xC0) {
+                std::string sz = std::to_string(size);
+                if (imm == 0xE1) o << R(src) << " = xchg<" << sz << ">(" << addr << ", " << R(src) << ");";
+                else if (imm == 0xF1) o << "r0 = cmpxchg<" << sz << ">(" << addr << ", r0, " << R(src) << ");";
+                else {
+                    int b = imm & ~1;
+                    const char *ag = b == 0x00 ? "AG_ADD" : b == 0x40 ? "AG_OR" : b == 0x50 ? "AG_AND" : "AG_XOR";
+                    if (imm & 1) o << R(src) << " = fetch_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ");";
+                    else o << "agg_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ", __activemask());";
+                }
+                break;
+            }
+            std::string v = cls == 3 ? R(src) : hex64((uint64_t)(int64_t)imm);
+            o << "store_sz<" << size << ">((uint8_t *)" << addr << ", " << v << ");";
+            break;
+        }
+        }
+        o << "\n";
+    }
+    o << "budget_trip:\n"
+      << "  atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);\n"
+      << "  set_status(env.stats, GX_E_BUDGET);\n"
+      << "  return 0;\n}\n\n";
+    out += o.str();
+    return GX_OK;
+}
+
+std::string fnv_hex(const std::string &s) {
+    uint64_t h = 1469598103934665603ULL;
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ULL;
+    }
+    char b[24];
+    snprintf(b, sizeof b, "%016llx", (unsigned long long)h);
+    return b;
+}
+
+struct Cached {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kernel = nullptr;
+};
+std::mutex cache_mu;
+std::map<std::string, Cached> cache;
+
+bool read_file(const std::string &path, std::vector<char> &out) {
+    FILE *f = fopen(path.c_str(), "rb");
+    if (!f) return false;
+    fseek(f, 0, SEEK_END);
+    long n = ftell(f);
+    fseek(f, 0, SEEK_SET);
+    out.resize(n > 0 ? (size_t)n : 0);
+    bool ok = n > 0 && fread(out.data(), 1, (size_t)n, f) == (size_t)n;
+    fclose(f);
+    return ok;
+}
+
+void write_file(const std::string &path, const std::vector<char> &data) {
+    std::string tmp = path + ".tmp" + std::to_string((unsigned long)getpid());
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
+    fclose(f);
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+}
+
+} // namespace
+
+std::string jit_source(const std::vector<const JitProgram *> &progs, std::string &log, int &rc) {
+    std::string src;
+    src += "#include \"gx_device.cuh\"\nnamespace gx {\n";
+    rc = GX_OK;
+    for (size_t i = 0; i < progs.size() && rc == GX_OK; i++) rc = gen_body(*progs[i], (int)i, src, log);
+    src += "} // namespace gx\n\nextern \"C\" __global__ void __launch_bounds__(256) gx_jit_kernel(gx::ExecParams P) {\n"
+           "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx::u64 *ctxw, bool valid, gx::u64 ev_idx) -> gx::u64 {\n";
+    if (progs.size() == 1) {
+        src += "    return gx::gx_body_0(env, ctxw, valid, ev_idx);\n";
+    } else {
+        src += "    switch (env.slot) {\n";
+        for (size_t i = 0; i < progs.size(); i++)
+            src += "    case " + std::to_string(i) + ": return gx::gx_body_" + std::to_string(i) +
+                   "(env, ctxw, valid, ev_idx);\n";
+        src += "    }\n    return 0;\n";
+    }
+    src += "  });\n}\n";
+    return src;
+}
+
+/* generated source -> cubin (disk cache first, then NVRTC) */
+int jit_cubin(const std::string &src, const std::string &key, std::vector<char> &cubin, std::string &log) {
+    const char *dir = getenv("GX_JIT_CACHE");
+    std::string path = dir && *dir ? std::string(dir) + "/" + key + ".cubin" : "";
+    if (!path.empty() && read_file(path, cubin)) return GX_OK;
+    Nvrtc &nv = nvrtc();
+    if (!nv.ok) {
+        log = "jit: " + nv.err;
+        return GX_E_NODEV;
+    }
+    const char *hdrs[] = {gx_embed_gx_h, gx_embed_gx_layout_h, gx_embed_gx_device_cuh};
+    const char *names[] = {"gx.h", "gx_layout.h", "gx_device.cuh"};
+    nvrtcProgram_ prog = nullptr;
+    if (nv.create(&prog, src.c_str(), "gx_prog.cu", 3, hdrs, names) != 0) {
+        log = "jit: nvrtcCreateProgram failed";
+        return GX_E_CUDA;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG", "-w"};
+    int rc = nv.compile(prog, 5, opts);
+    size_t ls = 0;
+    nv.log_size(prog, &ls);
+    std::string clog(ls, '\0');
+    if (ls) nv.log(prog, &clog[0]);
+    if (rc != 0) {
+        log = "jit: compile failed: " + clog.substr(0, 4000);
+        nv.destroy(&prog);
+        return GX_E_CUDA;
+    }
+    size_t cs = 0;
+    nv.cubin_size(prog, &cs);
+    cubin.resize(cs);
+    nv.cubin(prog, cubin.data());
+    nv.destroy(&prog);
+    if (!path.empty()) {
+        mkdir(dir, 0755);
+        write_file(path, cubin);
+    }
+    return GX_OK;
+}
+
+std::string jit_key(const std::string &src) {
+    return fnv_hex(src + gx_embed_gx_device_cuh + gx_embed_gx_layout_h + gx_embed_gx_h);
+}
+
+int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log) {
+    int rc;
+    const std::string src = jit_source(progs, log, rc);
+    if (rc) return rc;
+    const std::string key = jit_key(src);
+    {
+        std::lock_guard<std::mutex> g(cache_mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            out.kernel = it->second.kernel;
+            out.key = key;
+            return GX_OK;
+        }
+    }
+    std::vector<char> cubin;
+    rc = jit_cubin(src, key, cubin, log);
+    if (rc) return rc;
+    Cached c;
+    if (cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+        cudaLibraryGetKernel(&c.kernel, c.lib, "gx_jit_kernel") != cudaSuccess) {
+        cudaGetLastError();
+        log = "jit: loading the compiled program failed";
+        return GX_E_CUDA;
+    }
+    {
+        std::lock_guard<std::mutex> g(cache_mu);
+        cache[key] = c;
+    }
+    out.kernel = c.kernel;
+    out.key = key;
+    return GX_OK;
+}
+
+cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s) {
+    void *args[] = {(void *)&p};
+    return cudaLaunchKernel((const void *)k.kernel, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t jit_set_smem(JitKernel &k, size_t bytes) {
+    if (bytes <= k.smem_attr) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute((const void *)k.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) k.smem_attr = bytes;
+    return e;
+}
+
+cudaError_t jit_occupancy(const JitKernel &k, int block, size_t smem, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)k.kernel, block, smem);
+}
+
+} // namespace gx
+
+extern "C" int gx_jit_check(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                            const gx_prog_opts *opts, char *log, size_t log_len) {
+    if (!insns || !opts || (n_maps && !maps)) return GX_EINVAL;
+    gx::VerifyOut v;
+    int rc = gx::verify_program(insns, n, maps, n_maps, *opts, v);
+    std::string msg = v.log;
+    if (rc == GX_OK) {
+        gx::JitProgram jp;
+        jp.insns.assign(insns, insns + n);
+        jp.info = v.info;
+        jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        const std::string src = gx::jit_source({&jp}, msg, rc);
+        std::vector<char> cubin;
+        if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, msg.size());
+        memcpy(log, msg.data(), k);
+        log[k] = 0;
+    }
+    return rc;
+}

@@ -1262,6 +1262,9 @@ struct Verifier {
             if (s.r[i].t == NI) return fail(pc, "helper %d: argument R%d uninitialised", id, i);
         auto need_map = [&](int kind_ok) -> int {
             if (s.r[1].t != CMAP) return fail(pc, "helper %d: R1 must be a map", id);
+            InsnInfo &ii = out->info[pc];
+            if (ii.map == -1) ii.map = (int8_t)s.r[1].map;
+            else if (ii.map != (int8_t)s.r[1].map) ii.map = -2;
             u32 t = maps[s.r[1].map].type;
             if (kind_ok == 1 && t == GX_MAP_RINGBUF) return fail(pc, "helper %d: ring buffer given", id);
             if (kind_ok == 2 && t != GX_MAP_RINGBUF) return fail(pc, "helper %d: ring buffer expected", id);

@@ -74,6 +74,8 @@ _SIGS = {
                                ctypes.c_void_p]),
     "gx_verify": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                         ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_jit_check": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                           ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
                              ctypes.POINTER(ProgOpts), ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                              ctypes.c_size_t]),
@@ -105,6 +107,7 @@ def lib() -> ctypes.CDLL:
     """Load the native library (building it first if it is absent or stale)."""
     global _lib
     if _lib is None:
+        os.environ.setdefault("GX_JIT_CACHE", os.path.join(_build.BUILD, "jit"))
         path = _build.build()
         L = ctypes.CDLL(path)
         for name, (res, args) in _SIGS.items():
@@ -166,6 +169,21 @@ def verify(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, determin
     opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
     log = ctypes.create_string_buffer(1024)
     rc = lib().gx_verify(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), log, 1024)
+    return rc, log.value.decode()
+
+
+PROG_JIT = 1
+
+
+def jit_check(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, deterministic: bool = False,
+              insn_budget: int = 0) -> Tuple[int, str]:
+    """Host-only: verify and compile the specialised form (no device): (status, log)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    specs = (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"])
+                                                   for s in map_specs])
+    opts = ProgOpts(ctx_size, int(deterministic), insn_budget, PROG_JIT, 0)
+    log = ctypes.create_string_buffer(8192)
+    rc = lib().gx_jit_check(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), log, 8192)
     return rc, log.value.decode()
 
 
@@ -244,14 +262,14 @@ class Map:
 
 class Program:
     def __init__(self, ctx: Context, insns: np.ndarray, maps: Sequence[Map], ctx_size: int,
-                 deterministic: bool = False, insn_budget: int = 0) -> None:
+                 deterministic: bool = False, insn_budget: int = 0, jit: bool = False) -> None:
         insns = np.ascontiguousarray(insns, dtype=np.uint64)
         arr = (ctypes.c_void_p * max(1, len(maps)))(*[m.h for m in maps])
-        opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
-        log = ctypes.create_string_buffer(1024)
+        opts = ProgOpts(ctx_size, int(deterministic), insn_budget, PROG_JIT if jit else 0, 0)
+        log = ctypes.create_string_buffer(8192)
         h = ctypes.c_void_p()
         rc = lib().gx_verify_load(ctx.h, insns.ctypes.data, insns.size, arr, len(maps), ctypes.byref(opts),
-                                  ctypes.byref(h), log, 1024)
+                                  ctypes.byref(h), log, 8192)
         if rc:
             raise GxError(rc, "gx_verify_load", log.value.decode())
         self.h, self.ctx, self.maps, self.ctx_size = h, ctx, list(maps), ctx_size

@@ -76,7 +76,8 @@ def assert_same(gpu_snap, ora_snap) -> None:
 
 
 def run_both(ctx: gx.Context, prog: np.ndarray, specs: Sequence[dict], ctx_size: int, events: np.ndarray, *,
-             det: bool = True, launch: Optional[Tuple[int, int]] = None, idx_base: int = 0, check_r0: bool = True):
+             det: bool = True, launch: Optional[Tuple[int, int]] = None, idx_base: int = 0, check_r0: bool = True,
+             jit: bool = False):
     """Returns (gpu snapshot, oracle snapshot, r0 gpu, r0 oracle) after asserting equality."""
     import torch
 
@@ -84,7 +85,7 @@ def run_both(ctx: gx.Context, prog: np.ndarray, specs: Sequence[dict], ctx_size:
     om = O.maps_from_specs(specs)
     r0_o, _ = O.run(prog, om, events, ctx_size, want_r0=True, event_idx_base=idx_base)
     gm = gpu_maps(ctx, specs)
-    p = gx.Program(ctx, prog, gm, ctx_size, deterministic=det)
+    p = gx.Program(ctx, prog, gm, ctx_size, deterministic=det, jit=jit)
     dev = device_events(events)
     ret = torch.zeros(max(n, 1), dtype=torch.int64, device="cuda")
     p.run(dev, n, ret_out=ret, idx_base=idx_base, launch=launch)
