@@ -289,12 +289,12 @@ def run_latency(gx, torch, jit=True):
     return out
 
 
-def build_batch(gx, torch, ctx, sizes, seed=SEED):
+def build_batch(gx, torch, ctx, sizes, seed=SEED, jit=True):
     progs = P.batch_programs(seed=seed)
     items = []
     for p, ((prog_i, specs, cs), n) in enumerate(zip(progs, sizes)):
         maps = [gx.Map.from_spec(ctx, s) for s in specs]
-        prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True)
+        prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
         ev = gen.uniform_events(n, seed=seed ^ p)
         items.append((prog, maps, to_device(ev), n))
     return items
@@ -351,7 +351,7 @@ def run_served(gx, torch, seconds: float):
     loaded = []
     for prog_i, specs, cs in progs:
         maps = [gx.Map.from_spec(ctx, s) for s in specs]
-        loaded.append((gx.Program(ctx, prog_i, maps, cs, deterministic=True), maps))
+        loaded.append((gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=True), maps))
     lam = 20000.0
     n_req = int(lam * seconds)
     gaps = rng.exponential(1.0 / lam, n_req)
@@ -365,7 +365,7 @@ def run_served(gx, torch, seconds: float):
     res = {}
     for mode in ("plain", "served"):
         srv = gx.Server(ctx, mem_budget=8 << 30, max_inflight=4, max_items=4096, block=256, ept=4,
-                        plain=(mode == "plain"))
+                        plain=(mode == "plain"), progs=[p for p, _ in loaded])
         reqs = [(loaded[int(w)][0], pool.data_ptr() + int(s), int(n), None, i, float(o))
                 for i, (w, s, n, o) in enumerate(zip(which, starts, sizes, offs))]
         done = []

@@ -279,7 +279,9 @@ typedef struct gx_server_opts {
     uint32_t block;        /* persistent kernel block size, 64..256 (0 = 256) */
     uint32_t ept;          /* events per thread per chunk (0 = 4) */
     uint32_t plain;        /* 1: no batching, one gx_run_batch launch per request (the baseline) */
-    uint32_t reserved;
+    uint32_t n_progs;      /* programs registered up front (may be 0) */
+    gx_prog *const *progs; /* if every one of them was loaded with GX_PROG_JIT, ticks run one
+                              multi-program specialised kernel and only these programs are accepted */
 } gx_server_opts;
 
 typedef struct gx_completion {

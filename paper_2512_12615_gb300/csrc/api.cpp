@@ -453,6 +453,7 @@ int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *
         if (rc == GX_OK) {
             p->jp.insns.assign(insns, insns + n);
             p->jp.info = v.info;
+            p->jp.maps = specs;
             p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
             if (opts->flags & GX_PROG_JIT) {
                 rc = jit_build({&p->jp}, p->jk, msg);
@@ -660,7 +661,7 @@ int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_lau
     if (rc == GX_OK) {
         const uint64_t sample = std::min<uint64_t>(n, 1ull << 24);
         const uint32_t blocks[] = {128, 256};
-        const uint32_t epts[] = {1, 2, 4, 8, 16};
+        const uint32_t epts[] = {1, 2, 4, 8, 16, 32, 64};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);

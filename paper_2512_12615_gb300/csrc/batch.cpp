@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <set>
@@ -47,8 +48,9 @@ struct Item {
     int64_t *ret_out;
 };
 
-/* cut items into chunks of `chunk_events`, largest item first */
-void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vector<gx_chunk> &out) {
+/* cut items into chunks of `chunk_events`, largest item first; slots: program -> slot of a multi-program kernel */
+void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vector<gx_chunk> &out,
+                 const std::map<gx_prog *, uint32_t> *slots = nullptr) {
     std::vector<size_t> order(items.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return items[a].n > items[b].n; });
@@ -66,6 +68,7 @@ void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vec
             c.idx_base = 0;
             c.image_bytes = it.prog->image_bytes;
             c.ctx_size = it.prog->opts.ctx_size;
+            c.pad = slots ? slots->at(it.prog) : 0;
             out.push_back(c);
         }
     }
@@ -82,6 +85,7 @@ struct Persist {
     uint64_t cap_chunks = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    gx::JitKernel *jk = nullptr; /* set: the persistent kernel is a multi-program specialised kernel */
 
     unsigned *cursor() { return (unsigned *)dmem; }
     unsigned *nchunks() { return (unsigned *)dmem + 1; }
@@ -104,10 +108,11 @@ struct Persist {
         area = (uint32_t)round_up(image_area, 16);
         max_ctx = ctx_max;
         smem = exec_smem(area, block, max_ctx);
-        int rc = ensure_smem(c, smem);
+        int rc = jk ? cuda_status(jit_set_smem(*jk, smem)) : ensure_smem(c, smem);
         if (rc) return rc;
         int occ = 0;
-        if (exec_occupancy((int)block, smem, &occ) != cudaSuccess || occ < 1) {
+        cudaError_t oe = jk ? jit_occupancy(*jk, (int)block, smem, &occ) : exec_occupancy((int)block, smem, &occ);
+        if (oe != cudaSuccess || occ < 1) {
             cudaGetLastError();
             return GX_E_CUDA;
         }
@@ -130,7 +135,8 @@ struct Persist {
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = GX_E_CUDA;
         if (rc == GX_OK) {
             cudaMemsetAsync(cursor(), 0, 4, cs);
-            launch_exec(P, grid, block, smem, cs);
+            if (jk) jit_launch(*jk, P, grid, block, smem, cs);
+            else launch_exec(P, grid, block, smem, cs);
             if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) rc = GX_E_CUDA;
         }
         if (rc == GX_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = GX_E_CUDA;
@@ -151,7 +157,30 @@ struct gx_batch {
     Persist persist;
     bool planned = false;
     gx_launch shape{};
+    /* all programs specialised: one kernel holding every distinct program, switched by slot */
+    gx::JitKernel jk;
+    std::map<gx_prog *, uint32_t> slots;
+    bool jit = false;
 };
+
+/* build the batch's multi-program kernel when every item's program is specialised */
+static int batch_jit(gx_batch *b) {
+    b->jit = !b->items.empty();
+    for (auto &it : b->items)
+        if (!it.prog->jit) b->jit = false;
+    if (!b->jit) return GX_OK;
+    std::vector<const gx::JitProgram *> progs;
+    b->slots.clear();
+    for (auto &it : b->items)
+        if (!b->slots.count(it.prog)) {
+            b->slots[it.prog] = (uint32_t)progs.size();
+            progs.push_back(&it.prog->jp);
+        }
+    std::string log;
+    int rc = gx::jit_build(progs, b->jk, log);
+    if (rc) b->jit = false;
+    return rc;
+}
 
 struct gx_server {
     struct Req {
@@ -187,6 +216,10 @@ struct gx_server {
     std::set<gx_map *> maps_seen;
     uint64_t map_bytes = 0;
     int error = GX_OK;
+    /* registered specialised programs: one multi-program kernel for every tick */
+    gx::JitKernel jk;
+    std::map<gx_prog *, uint32_t> prog_slot;
+    bool jit = false;
 
     void run();
 };
@@ -216,7 +249,8 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept) {
         area = std::max(area, it.prog->image_bytes);
         max_ctx = std::max(max_ctx, it.prog->opts.ctx_size);
     }
-    make_chunks(b->items, (uint64_t)block * ept, b->chunks);
+    make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr);
+    b->persist.jk = b->jit ? &b->jk : nullptr;
     int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size());
     if (rc) return rc;
     unsigned nch = (unsigned)b->chunks.size();
@@ -232,6 +266,8 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
     if (!b || b->items.empty()) return GX_EINVAL;
     if (b->chunks.size() > 0x7FFFFFFF) return GX_E2BIG;
     cudaStream_t s = (cudaStream_t)stream;
+    int jrc = batch_jit(b);
+    if (jrc) return jrc;
     if (lp) {
         uint32_t blk = lp->block ? lp->block : 256, ept = lp->ept ? lp->ept : 4;
         if (blk < 64 || blk > GX_MAX_BLOCK || blk % 32 || ept < 1 || ept > 64) return GX_EINVAL;
@@ -321,10 +357,36 @@ int gx_server_create(gx_ctx *c, const gx_server_opts *o, gx_server **out) {
     if (opts.max_inflight > 8 || opts.max_items > 4096 || opts.block < 64 || opts.block > GX_MAX_BLOCK ||
         opts.block % 32 || opts.ept > 64)
         return GX_EINVAL;
+    if (opts.n_progs && !opts.progs) return GX_EINVAL;
     gx_server *s = new gx_server();
     s->ctx = c;
     s->opts = opts;
     s->chunk_events = (uint64_t)opts.block * opts.ept;
+    if (opts.n_progs) {
+        bool all_jit = true;
+        std::vector<const gx::JitProgram *> progs;
+        for (uint32_t i = 0; i < opts.n_progs; i++) {
+            gx_prog *p = opts.progs[i];
+            if (!p || p->ctx != c) {
+                delete s;
+                return GX_EINVAL;
+            }
+            if (!p->jit) all_jit = false;
+            if (!s->prog_slot.count(p)) {
+                s->prog_slot[p] = (uint32_t)progs.size();
+                progs.push_back(&p->jp);
+            }
+        }
+        if (all_jit && !opts.plain) {
+            std::string log;
+            int rc = gx::jit_build(progs, s->jk, log);
+            if (rc) {
+                delete s;
+                return rc;
+            }
+            s->jit = true;
+        }
+    }
     s->slots.resize(opts.max_inflight);
     for (auto &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -349,6 +411,7 @@ int gx_server_create(gx_ctx *c, const gx_server_opts *o, gx_server **out) {
 int gx_server_submit(gx_server *s, gx_prog *p, const void *events, uint64_t n, int64_t *ret_out, uint64_t tag,
                      double t_arrival) {
     if (!s || !p || p->ctx != s->ctx || (!events && n) || (((uintptr_t)events) & 15)) return GX_EINVAL;
+    if (s->jit && !s->prog_slot.count(p)) return GX_EINVAL; /* not part of the server's kernel */
     gx_server::Req r{p, events, n, ret_out, tag, t_arrival > 0 ? t_arrival : now_s(), n * p->opts.ctx_size};
     std::lock_guard<std::mutex> g(s->mu);
     for (auto *m : p->maps)
@@ -496,11 +559,12 @@ void gx_server::run() {
             }
             if (!sl.persist.exec || area > sl.persist.area || max_ctx > sl.persist.max_ctx) {
                 cudaStreamSynchronize(sl.stream);
+                sl.persist.jk = jit ? &jk : nullptr;
                 rc = sl.persist.build(ctx, opts.block, std::max(area, sl.persist.area),
                                       std::max(max_ctx, sl.persist.max_ctx), cap_chunks);
             }
             std::vector<gx_chunk> table;
-            make_chunks(items, chunk_events, table);
+            make_chunks(items, chunk_events, table, jit ? &prog_slot : nullptr);
             if (rc == GX_OK) {
                 memcpy(sl.host_table, table.data(), table.size() * sizeof(gx_chunk));
                 /* the count travels in the same pinned buffer, in the entry after the table */

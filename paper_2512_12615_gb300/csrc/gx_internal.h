@@ -20,6 +20,9 @@ struct InsnInfo {
     uint8_t kind = MK_NONE; /* region of a load / store / atomic */
     int16_t off = 0;        /* MK_CTX: absolute ctx offset; MK_STACK: offset from the frame top */
     int8_t map = -1;        /* helper call: map index in R1 on every path, -2 if it varies */
+    int16_t a2 = ARG_UNSET; /* helper call: constant stack offset of R2 on every path (else ARG_VARIES) */
+    int16_t a3 = ARG_UNSET; /* same for R3 */
+    static const int16_t ARG_UNSET = 32767, ARG_VARIES = 32766;
 };
 
 struct VerifyOut {

@@ -16,6 +16,7 @@ namespace gx {
 struct JitProgram {
     std::vector<uint64_t> insns;
     std::vector<InsnInfo> info;
+    std::vector<gx_map_spec> maps; /* layouts become compile-time constants */
     uint64_t budget = 1ull << 16;
 };
 

@@ -491,6 +491,7 @@ extern "C" int gx_jit_check(const uint64_t *insns, uint32_t n, const gx_map_spec
         gx::JitProgram jp;
         jp.insns.assign(insns, insns + n);
         jp.info = v.info;
+        jp.maps.assign(maps, maps + n_maps);
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
         const std::string src = gx::jit_source({&jp}, msg, rc);
         std::vector<char> cubin;

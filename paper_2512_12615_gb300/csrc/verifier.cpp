@@ -1265,6 +1265,13 @@ struct Verifier {
             InsnInfo &ii = out->info[pc];
             if (ii.map == -1) ii.map = (int8_t)s.r[1].map;
             else if (ii.map != (int8_t)s.r[1].map) ii.map = -2;
+            auto note_arg = [&](int16_t &slot, const Reg &r) {
+                int16_t v = (r.t == STK && is_const(r)) ? (int16_t)r.smin : InsnInfo::ARG_VARIES;
+                if (slot == InsnInfo::ARG_UNSET) slot = v;
+                else if (slot != v) slot = InsnInfo::ARG_VARIES;
+            };
+            note_arg(ii.a2, s.r[2]);
+            note_arg(ii.a3, s.r[3]);
             u32 t = maps[s.r[1].map].type;
             if (kind_ok == 1 && t == GX_MAP_RINGBUF) return fail(pc, "helper %d: ring buffer given", id);
             if (kind_ok == 2 && t != GX_MAP_RINGBUF) return fail(pc, "helper %d: ring buffer expected", id);

@@ -46,7 +46,7 @@ class RunStats(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget", u64), ("max_inflight", u32), ("max_items", u32), ("block", u32), ("ept", u32),
-                ("plain", u32), ("reserved", u32)]
+                ("plain", u32), ("n_progs", u32), ("progs", ctypes.POINTER(ctypes.c_void_p))]
 
 
 class Completion(ctypes.Structure):
@@ -332,8 +332,9 @@ class Batch:
 
 class Server:
     def __init__(self, ctx: Context, mem_budget: int = 0, max_inflight: int = 2, max_items: int = 1024,
-                 block: int = 256, ept: int = 4, plain: bool = False) -> None:
-        opts = ServerOpts(mem_budget, max_inflight, max_items, block, ept, int(plain), 0)
+                 block: int = 256, ept: int = 4, plain: bool = False, progs: Sequence["Program"] = ()) -> None:
+        self._progs = (ctypes.c_void_p * max(1, len(progs)))(*[p.h for p in progs])
+        opts = ServerOpts(mem_budget, max_inflight, max_items, block, ept, int(plain), len(progs), self._progs)
         h = ctypes.c_void_p()
         check(lib().gx_server_create(ctx.h, ctypes.byref(opts), ctypes.byref(h)), "gx_server_create")
         self.h = h
