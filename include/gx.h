@@ -149,6 +149,27 @@ uint64_t gx_map_bytes(const gx_map *map);
  */
 int gx_map_read(gx_map *map, void *host_out, uint64_t cap_bytes, uint64_t *n_out, void *stream);
 /*
+ * Hash-map snapshot that allocates nothing.  The paper has no counterpart: this is for
+ * callers that cannot call cudaMalloc, for example a control plane whose device-memory
+ * budget is already used up, or a monitoring thread that must not add allocation (and
+ * the device synchronisation cudaMalloc may bring) while the GPU serves requests.
+ * gx_map_read compacts into a per-map scratch buffer that it allocates on first use;
+ * this variant compacts into one fixed, file-scope device array of
+ * GX_NOALLOC_SCRATCH_BYTES (256 bytes of counter + packed pairs) that every device
+ * loading the library keeps until the process exits.  Same output format as
+ * gx_map_read for hash maps; synchronises `stream`.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call shares the array and clears its counter: calls whose GPU work overlaps
+ *     (other streams or host threads) race on it.
+ *   - GX_EINVAL for array or ring-buffer maps.  GX_E2BIG, with *n_out = the live pair
+ *     count and nothing copied, when the live pairs exceed the array
+ *     ((GX_NOALLOC_SCRATCH_BYTES - 256) / (key_size + value_size) pairs) or cap_bytes.
+ */
+#define GX_NOALLOC_SCRATCH_BYTES (4u << 20)
+int gx_map_read_noalloc(gx_map *map, void *host_out, uint64_t cap_bytes, uint64_t *n_out, void *stream);
+/*
  * Restore a map from host memory (the inverse of gx_map_read); synchronises `stream`.
  *   array: exactly max_entries*value_size bytes, overwriting every value.
  *   hash:  packed {key, value} pairs, inserted or overwritten (BPF_ANY semantics);

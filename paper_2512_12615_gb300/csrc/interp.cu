@@ -26,8 +26,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gx_device.cuh"
 #include "gx_kernels.h"
+#include "gx_runtime.h"
 
 namespace gx {
 
@@ -361,3 +364,73 @@ cudaError_t launch_hash_insert(const gx_dmap &m, const uint8_t *in, uint64_t npa
 }
 
 } // namespace gx
+
+/* ------------------------------------------------------------------ snapshot without allocation */
+/*
+ * Scratch for gx_map_read_noalloc, fixed at GX_NOALLOC_SCRATCH_BYTES: bytes [0, 256) hold the
+ * pair counter, the packed {key, value} pairs follow.  Every device that loads the library
+ * keeps this array until the process exits.  All calls share it, so calls whose GPU work
+ * overlaps (other streams, other host threads) race on it.
+ */
+static __device__ __align__(256) unsigned char gx_noalloc_scratch[GX_NOALLOC_SCRATCH_BYTES];
+
+namespace gx {
+namespace {
+std::mutex noalloc_mu;
+void *noalloc_ptr[64];
+bool noalloc_ready[64];
+} // namespace
+} // namespace gx
+
+extern "C" int gx_map_read_noalloc(gx_map *m, void *host_out, uint64_t cap_bytes, uint64_t *n_out, void *stream) {
+    using namespace gx;
+    if (!m || (!host_out && cap_bytes)) return GX_EINVAL;
+    if (m->d.type != GX_MAP_HASH) return GX_EINVAL;
+    const uint64_t pair = (uint64_t)m->d.key_size + m->d.value_size;
+    const uint64_t cap_pairs = (GX_NOALLOC_SCRATCH_BYTES - 256) / pair;
+    if (cap_pairs == 0) return GX_E2BIG;
+    const int dev = m->ctx->device;
+    if (dev < 0 || dev >= 64) return GX_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return GX_E_CUDA;
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess) return GX_E_CUDA;
+    int rc = GX_OK;
+    void *base = nullptr;
+    {
+        /* one-time set-up per device, with that device current: the array's device address */
+        std::lock_guard<std::mutex> g(noalloc_mu);
+        if (!noalloc_ready[dev]) {
+            if (cudaGetSymbolAddress(&noalloc_ptr[dev], gx_noalloc_scratch) != cudaSuccess) {
+                cudaGetLastError();
+                rc = GX_E_CUDA;
+            } else {
+                noalloc_ready[dev] = true;
+            }
+        }
+        base = noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long cnt = 0;
+    if (rc == GX_OK) {
+        unsigned long long *count = (unsigned long long *)base;
+        uint8_t *pairs = (uint8_t *)base + 256;
+        if (cudaMemsetAsync(count, 0, 8, s) != cudaSuccess ||
+            launch_hash_compact(m->d, pairs, count, cap_pairs, s) != cudaSuccess ||
+            cudaMemcpyAsync(&cnt, count, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            rc = GX_E_CUDA;
+        } else if (cnt > cap_pairs) {
+            rc = GX_E2BIG; /* the live pairs do not fit the fixed scratch: nothing copied */
+        } else if (cnt * pair > cap_bytes) {
+            rc = GX_E2BIG;
+        } else if (cnt && (cudaMemcpyAsync(host_out, pairs, cnt * pair, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                           cudaStreamSynchronize(s) != cudaSuccess)) {
+            cudaGetLastError();
+            rc = GX_E_CUDA;
+        }
+    }
+    if (n_out) *n_out = cnt;
+    if (cur != dev) cudaSetDevice(cur);
+    return rc;
+}

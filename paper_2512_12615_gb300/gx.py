@@ -68,6 +68,7 @@ _SIGS = {
     "gx_map_destroy": (i32, [ctypes.c_void_p]),
     "gx_map_bytes": (u64, [ctypes.c_void_p]),
     "gx_map_read": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(u64), ctypes.c_void_p]),
+    "gx_map_read_noalloc": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(u64), ctypes.c_void_p]),
     "gx_map_write": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p]),
     "gx_map_clear": (i32, [ctypes.c_void_p, ctypes.c_void_p]),
     "gx_ringbuf_drain": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
