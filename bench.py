@@ -146,7 +146,7 @@ def run_headline(args, gx, torch, dist_env, jit=True):
     ctx = gx.Context(torch.cuda.current_device())
     maps = [gx.Map.from_spec(ctx, s) for s in specs]
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
-    block, ept = prog.autotune(dev, C2_EVENTS, stream=sid)
+    block, ept, shards = prog.autotune(dev, C2_EVENTS, stream=sid)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         prog.run(dev, C2_EVENTS, stream=sid)
@@ -213,7 +213,7 @@ def run_headline(args, gx, torch, dist_env, jit=True):
                      "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
                      "kernel": "gx_jit_kernel" if jit else "gx_exec_kernel", "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": round(avg_launch, 4)},
-        "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept},
+        "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept, "shards": shards},
         "insns_per_event": round(insns_per_event, 2),
         "Minsns_per_s": round(value * insns_per_event, 1),
     }

@@ -224,6 +224,22 @@ int gx_jit_check(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *map
  */
 int gx_verify(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
               const gx_prog_opts *opts, char *log, size_t log_len);
+/*
+ * What the verifier proved about an accepted program (host only, no device needed).
+ * combinable_maps: bit m is set when the program changes map m's values only through
+ * non-fetching commutative updates (BPF_ATOMIC ADD / OR / AND / XOR without FETCH, the
+ * atomic max / min helpers) at constant offsets, one operation per 4-byte word, and never
+ * loads, stores, exchanges or overwrites them or hands them to a helper.  Such updates
+ * may be combined per thread block in shared memory before they reach device memory
+ * (gx_launch.shards); the map's final contents are the same.  Returns as gx_verify.
+ */
+typedef struct gx_analysis {
+    uint64_t insns_processed; /* instructions the verifier explored */
+    uint32_t stack_depth;     /* deepest stack byte the program touches */
+    uint32_t combinable_maps; /* bit m: see above */
+} gx_analysis;
+int gx_analyze(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+               const gx_prog_opts *opts, gx_analysis *out, char *log, size_t log_len);
 /* Verify, decode and upload a program; it holds a reference on each map. */
 int gx_verify_load(gx_ctx *ctx, const uint64_t *insns, uint32_t n_insns, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len);
@@ -233,11 +249,16 @@ uint32_t gx_prog_uops(const gx_prog *prog);
 
 /* ---------------------------------------------------------------- runs */
 typedef struct gx_launch {
-    uint32_t block; /* threads per block: 64..1024, multiple of 32; 0 = tuned/default */
-    uint32_t ept;   /* events per thread: 1..64; 0 = tuned/default */
-    uint32_t grid;  /* blocks; 0 = enough for n */
-    uint32_t reserved;
+    uint32_t block;  /* threads per block: 64..1024, multiple of 32; 0 = tuned/default */
+    uint32_t ept;    /* events per thread: 1..64; 0 = tuned/default */
+    uint32_t grid;   /* blocks; 0 = enough for n */
+    uint32_t shards; /* map-sharding width of load-time specialised programs (GX_PROG_JIT): updates of
+                        combinable maps (gx_analyze) are first combined in shared memory per block,
+                        small array maps whole, other maps in a cache of 2^shards entries (2..10, capped
+                        per map by its value size); GX_SHARDS_OFF sends every update to device memory
+                        (warp-aggregated); 0 = tuned/default.  Ignored by the interpreter. */
 } gx_launch;
+#define GX_SHARDS_OFF 255u
 
 /*
  * Run the program once per event over n records at events_dev (n * ctx_size bytes,

@@ -107,6 +107,13 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     if (block < 32 || block > GX_MAX_BLOCK || block % 32 || ept < 1 || ept > 64) return GX_EINVAL;
     uint32_t area = (uint32_t)round_up(image_bytes, 16);
     uint64_t smem = exec_smem(area, block, p->opts.ctx_size);
+    uint32_t wc = 0, shard_off = 0;
+    if (lp.shards && lp.shards != GX_SHARDS_OFF && (lp.shards < 2 || lp.shards > 10)) return GX_EINVAL;
+    if (p->jit && p->jk.shard_bytes && lp.shards != GX_SHARDS_OFF) {
+        wc = lp.shards ? lp.shards : p->jk.wc_max_bits;
+        shard_off = (uint32_t)round_up(smem, 16);
+        smem = shard_off + p->jk.shard_bytes;
+    }
     int rc = ensure_smem(p->ctx, smem);
     if (rc) return rc;
     uint64_t per_block = (uint64_t)block * ept;
@@ -125,6 +132,8 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     P.n = n;
     P.idx_base = idx_base;
     P.ret_out = (long long *)ret_out;
+    P.wc_bits = wc;
+    P.shard_off = shard_off;
     if (p->jit) {
         rc = cuda_status(jit_set_smem(p->jk, smem));
         if (rc == GX_OK) rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s));
@@ -145,7 +154,7 @@ int tuned_launch(gx_prog *p, uint64_t n, gx_launch *out) {
     out->block = 256;
     out->ept = n >= (1ull << 24) ? 8 : 4;
     out->grid = 0;
-    out->reserved = 0;
+    out->shards = 0;
     return 0;
 }
 
@@ -430,6 +439,26 @@ int gx_verify(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32
     return rc;
 }
 
+int gx_analyze(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps, const gx_prog_opts *opts,
+               gx_analysis *out, char *log, size_t log_len) {
+    if (!insns || !opts || !out || (n_maps && !maps)) return GX_EINVAL;
+    VerifyOut v;
+    int rc = verify_program(insns, n, maps, n_maps, *opts, v);
+    memset(out, 0, sizeof *out);
+    if (rc == GX_OK) {
+        out->insns_processed = v.insns_processed;
+        out->stack_depth = v.stack_depth;
+        for (uint32_t m = 0; m < n_maps && m < v.map_use.size(); m++)
+            if (v.map_use[m].combinable() && maps[m].type != GX_MAP_RINGBUF) out->combinable_maps |= 1u << m;
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, v.log.size());
+        memcpy(log, v.log.data(), k);
+        log[k] = 0;
+    }
+    return rc;
+}
+
 int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len) {
     if (!c || !insns || !opts || !out || (n_maps && !maps)) return GX_EINVAL;
@@ -454,6 +483,7 @@ int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *
             p->jp.insns.assign(insns, insns + n);
             p->jp.info = v.info;
             p->jp.maps = specs;
+            p->jp.use = v.map_use;
             p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
             if (opts->flags & GX_PROG_JIT) {
                 rc = jit_build({&p->jp}, p->jk, msg);
@@ -667,9 +697,15 @@ int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_lau
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         uint32_t img_bytes = (uint32_t)round_up(sizeof(gx_dprog_hdr) + descs.size() * sizeof(gx_dmap) + p->uops.size() * 8, 16);
+        /* map-sharding width: off, and the combining caches at 64 and at their widest */
+        std::vector<uint32_t> widths = {0};
+        if (p->jit && p->jk.shard_bytes) {
+            widths = {GX_SHARDS_OFF, 0};
+            if (p->jk.wc_max_bits > 6) widths.push_back(6);
+        }
         for (uint32_t b : blocks) {
-            for (uint32_t e : epts) {
-                gx_launch l = {b, e, 0, 0};
+            for (uint32_t e : epts) for (uint32_t w : widths) {
+                gx_launch l = {b, e, 0, w};
                 if (launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s)) continue;
                 cudaEventRecord(e0, s);
                 for (int r = 0; r < 3; r++) launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s);

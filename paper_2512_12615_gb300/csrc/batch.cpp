@@ -101,13 +101,20 @@ struct Persist {
         dbytes = 0;
     }
 
-    int build(gx_ctx *c, uint32_t blk, uint32_t image_area, uint32_t ctx_max, uint64_t chunks) {
+    /* shards: gx_launch.shards (0 = widest combining cache of the specialised kernel, GX_SHARDS_OFF = none) */
+    int build(gx_ctx *c, uint32_t blk, uint32_t image_area, uint32_t ctx_max, uint64_t chunks, uint32_t shards = 0) {
         release();
         ctx = c;
         block = blk;
         area = (uint32_t)round_up(image_area, 16);
         max_ctx = ctx_max;
         smem = exec_smem(area, block, max_ctx);
+        uint32_t wc = 0, shard_off = 0;
+        if (jk && jk->shard_bytes && shards != GX_SHARDS_OFF) {
+            wc = shards ? shards : jk->wc_max_bits;
+            shard_off = (uint32_t)round_up(smem, 16);
+            smem = shard_off + jk->shard_bytes;
+        }
         int rc = jk ? cuda_status(jit_set_smem(*jk, smem)) : ensure_smem(c, smem);
         if (rc) return rc;
         int occ = 0;
@@ -129,6 +136,8 @@ struct Persist {
         P.chunks = table();
         P.cursor = cursor();
         P.nchunks_dev = nchunks();
+        P.wc_bits = wc;
+        P.shard_off = shard_off;
         cudaStream_t cs;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return GX_E_CUDA;
         rc = GX_OK;
@@ -243,7 +252,7 @@ int gx_batch_add(gx_batch *b, gx_prog *p, const void *events, uint64_t n, int64_
     return GX_OK;
 }
 
-static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept) {
+static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t shards) {
     uint32_t area = 0, max_ctx = 8;
     for (auto &it : b->items) {
         area = std::max(area, it.prog->image_bytes);
@@ -251,14 +260,14 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept) {
     }
     make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr);
     b->persist.jk = b->jit ? &b->jk : nullptr;
-    int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size());
+    int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size(), shards);
     if (rc) return rc;
     unsigned nch = (unsigned)b->chunks.size();
     if (cudaMemcpy(b->persist.table(), b->chunks.data(), b->chunks.size() * sizeof(gx_chunk),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->persist.nchunks(), &nch, 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return GX_E_CUDA;
-    b->shape = gx_launch{block, ept, b->persist.grid, 0};
+    b->shape = gx_launch{block, ept, b->persist.grid, shards};
     return GX_OK;
 }
 
@@ -271,7 +280,8 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
     if (lp) {
         uint32_t blk = lp->block ? lp->block : 256, ept = lp->ept ? lp->ept : 4;
         if (blk < 64 || blk > GX_MAX_BLOCK || blk % 32 || ept < 1 || ept > 64) return GX_EINVAL;
-        int rc = batch_plan_shape(b, blk, ept);
+        if (lp->shards && lp->shards != GX_SHARDS_OFF && (lp->shards < 2 || lp->shards > 10)) return GX_EINVAL;
+        int rc = batch_plan_shape(b, blk, ept, lp->shards);
         if (rc == GX_OK) b->planned = true;
         return rc;
     }
@@ -299,9 +309,11 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
         cudaEventCreate(&e1);
         const uint32_t blocks[] = {128, 256};
         const uint32_t epts[] = {2, 4, 8, 16};
+        std::vector<uint32_t> widths = {0};
+        if (b->jit && b->jk.shard_bytes) widths = {GX_SHARDS_OFF, 0};
         for (uint32_t blk : blocks)
-            for (uint32_t ept : epts) {
-                if (batch_plan_shape(b, blk, ept) != GX_OK) continue;
+            for (uint32_t ept : epts) for (uint32_t w : widths) {
+                if (batch_plan_shape(b, blk, ept, w) != GX_OK) continue;
                 b->persist.launch(s); /* warm-up */
                 cudaEventRecord(e0, s);
                 b->persist.launch(s);
@@ -311,7 +323,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = gx_launch{blk, ept, 0, 0};
+                    best = gx_launch{blk, ept, 0, w};
                 }
             }
         cudaEventDestroy(e0);
@@ -324,7 +336,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
     }
     for (size_t i = 0; i < maps.size(); i++) dfree(b->ctx, saved[i], maps[i]->dbytes);
     if (rc) return rc;
-    rc = batch_plan_shape(b, best.block, best.ept);
+    rc = batch_plan_shape(b, best.block, best.ept, best.shards);
     if (rc == GX_OK) b->planned = true;
     return rc;
 }

@@ -521,8 +521,94 @@ struct ExecEnv {
     const gx_dmap *maps;
     u64 *stats;
     u64 budget;
-    u32 slot; /* which program of a multi-program specialised kernel (chunk.pad); 0 in plain mode */
+    u32 slot;      /* which program of a multi-program specialised kernel (chunk.pad); 0 in plain mode */
+    u32 wc_bits;   /* block-private combining: log2 cache entries per map, 0 = off */
+    uint8_t *shard; /* the block's combining area (shared memory) */
 };
+
+/* ------------------------------------------------------------------ block-private combining */
+/*
+ * Hierarchical map updates (the per-SM shards merged into the global map of Sec. 5.3):
+ * when the verifier proved that a program only updates a map's values with non-fetching
+ * commutative operations, those updates first land in shared memory and each block adds
+ * its totals to device memory once, when it finishes (or, in the persistent kernel, when
+ * its chunk ends).  Small array maps get a whole private copy; other maps get a cache of
+ * 2^wc_bits entries tagged by value address, and an update whose entry is held by another
+ * value goes straight to device memory.  Every operation here is per lane: no warp
+ * collectives.  A 64-bit add is split into 32-bit halves (the low half's carry is added
+ * into the high half), since 32-bit shared atomics are native.
+ */
+__device__ __forceinline__ u32 sh_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ u32 sh_atom_add(u32 a, u32 v) {
+    u32 r;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(r) : "r"(a), "r"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ void sh_red(u32 a, u32 v, int op) {
+    if (op == AG_ADD) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+    else if (op == AG_OR) asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+    else if (op == AG_AND) asm volatile("red.shared.and.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+    else asm volatile("red.shared.xor.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+/* identity of an operation on 32 / 64 bits */
+template <int OP>
+__device__ __forceinline__ u64 wc_ident() {
+    return (OP == AG_AND || OP == AG_MIN) ? ~0ull : 0ull;
+}
+
+/* apply v to the shared word at a (8-byte aligned for SZ == 8) */
+template <int OP, int SZ>
+__device__ __forceinline__ void sh_update(u32 a, u64 v) {
+    if (SZ == 4) {
+        if (OP == AG_ADD || ((u32)v != (u32)wc_ident<OP>())) sh_red(a, (u32)v, OP);
+        return;
+    }
+    if (OP == AG_ADD) {
+        u32 lo = (u32)v, hi = (u32)(v >> 32);
+        u32 old = sh_atom_add(a, lo);
+        hi += (old + lo < old) ? 1u : 0u;
+        if (hi) sh_red(a + 4, hi, AG_ADD);
+    } else if (OP == AG_MAX) {
+        asm volatile("red.shared.max.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+    } else if (OP == AG_MIN) {
+        asm volatile("red.shared.min.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+    } else {
+        u32 lo = (u32)v, hi = (u32)(v >> 32), id = (u32)wc_ident<OP>();
+        if (lo != id) sh_red(a, lo, OP);
+        if (hi != id) sh_red(a + 4, hi, OP);
+    }
+}
+
+/* fill n 32-bit words of a combining area with identities: word i gets ident(i % wpv) */
+__device__ __forceinline__ void wc_fill(uint8_t *area, u32 n_words, u32 wpv, u64 and_mask) {
+    u32 *w = (u32 *)area;
+    for (u32 i = threadIdx.x; i < n_words; i += blockDim.x) w[i] = ((and_mask >> (i % wpv)) & 1) ? ~0u : 0u;
+}
+
+/*
+ * Cache lookup for the value at `base`: the entry's accumulator words, claiming a free
+ * entry if needed, or nullptr when the entry holds another value.  tags: 2^max_bits u64.
+ */
+__device__ __forceinline__ uint8_t *wc_entry(uint8_t *tags, uint8_t *acc, u32 bits, u32 stride, u64 base) {
+    const u32 h = (u32)((base * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+    const u32 ta = sh_addr(tags) + h * 8u;
+    u64 t;
+    asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(t) : "r"(ta));
+    if (t == 0) {
+        asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(t) : "r"(ta), "l"(0ull), "l"(base) : "memory");
+        if (t == 0) t = base;
+    }
+    return t == base ? acc + (size_t)h * stride : nullptr;
+}
+
+/* device-memory form of a combined total (the block's flush) */
+template <int OP, int SZ>
+__device__ __forceinline__ void wc_flush_word(void *g, u64 v) {
+    if (v == (SZ == 4 ? (wc_ident<OP>() & 0xFFFFFFFFull) : wc_ident<OP>())) return;
+    plain_atomic<OP, SZ>(g, v);
+}
 
 /*
  * The launch skeleton shared by the interpreter and by load-time specialised programs.
@@ -533,8 +619,8 @@ struct ExecEnv {
  * its 32 records into shared memory, then `run_event` executes one event per lane and
  * returns R0.
  */
-template <typename RunEvent>
-__device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_event) {
+template <typename RunEvent, typename Init, typename Flush>
+__device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_event, Init wc_init, Flush wc_flush) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ u32 s_chunk;
     __shared__ const uint8_t *s_image;
@@ -550,6 +636,12 @@ __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_eve
         env.stats = hdr->stats;
         env.budget = hdr->budget;
         env.slot = 0;
+        env.wc_bits = P.wc_bits;
+        env.shard = smem + P.shard_off;
+        if (P.wc_bits) {
+            wc_init(env);
+            __syncthreads();
+        }
         const u32 cw = P.ctx_size / 8;
         u64 *ctxw = ctx_all + warp * cw * 32;
         const u64 tile0 = (u64)blockIdx.x * blockDim.x * P.ept;
@@ -562,6 +654,10 @@ __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_eve
             u64 r0 = run_event(env, ctxw, valid, P.idx_base + idx);
             if (valid && P.ret_out) P.ret_out[idx] = (long long)r0;
             __syncwarp();
+        }
+        if (P.wc_bits) {
+            __syncthreads();
+            wc_flush(env);
         }
         return;
     }
@@ -586,6 +682,12 @@ __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_eve
         env.stats = hdr->stats;
         env.budget = hdr->budget;
         env.slot = (u32)ch.pad;
+        env.wc_bits = P.wc_bits;
+        env.shard = smem + P.shard_off;
+        if (P.wc_bits) {
+            wc_init(env);
+            __syncthreads();
+        }
         const u32 cw = ch.ctx_size / 8;
         u64 *ctxw = ctx_all + warp * cw * 32;
         for (u64 first = ch.begin + (u64)warp * 32; first < ch.end; first += (u64)warps * 32) {
@@ -596,7 +698,17 @@ __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_eve
             if (valid && ch.ret_out) ch.ret_out[idx] = (long long)r0;
             __syncwarp();
         }
+        if (P.wc_bits) {
+            __syncthreads();
+            wc_flush(env);
+        }
     }
+}
+
+/* the interpreter: no block-private combining */
+template <typename RunEvent>
+__device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_event) {
+    exec_tiles(P, run_event, [](const ExecEnv &) {}, [](const ExecEnv &) {});
 }
 
 } // namespace gx

@@ -22,7 +22,30 @@ struct InsnInfo {
     int8_t map = -1;        /* helper call: map index in R1 on every path, -2 if it varies */
     int16_t a2 = ARG_UNSET; /* helper call: constant stack offset of R2 on every path (else ARG_VARIES) */
     int16_t a3 = ARG_UNSET; /* same for R3 */
+    int8_t vmap = -1;       /* update of map memory (atomic, atomic max/min helper): the map on every path,
+                               -2 if it varies or is not always a map value */
+    int16_t voff = ARG_UNSET; /* ... and the constant byte offset within the value (else ARG_VARIES) */
     static const int16_t ARG_UNSET = 32767, ARG_VARIES = 32766;
+};
+
+/*
+ * How a program touches the values of one map.  Updates that are non-fetching and
+ * commutative (ADD / OR / AND / XOR atomics, the atomic max / min helpers) can be combined
+ * per block in shared memory before they reach HBM, provided nothing else reads or
+ * overwrites those values and every 4-byte word has a single operation.
+ */
+enum UpdClass : uint8_t { UC_NONE = 0, UC_ADD, UC_OR, UC_AND, UC_XOR, UC_MAX, UC_MIN, UC_W8 = 0x10 };
+struct MapUse {
+    bool other = false;      /* loaded, stored, exchanged, fetched, overwritten by update, passed to a helper,
+                                or updated at a variable offset */
+    bool mixed = false;      /* a word updated by two different operations or widths */
+    std::vector<uint8_t> op; /* per 4-byte word of the value: UpdClass | UC_W8 for 8-byte operations */
+    bool combinable() const {
+        if (other || mixed) return false;
+        for (uint8_t c : op)
+            if (c) return true;
+        return false;
+    }
 };
 
 struct VerifyOut {
@@ -31,6 +54,7 @@ struct VerifyOut {
     uint64_t insns_processed = 0;
     uint64_t states_stored = 0;
     uint32_t stack_depth = 0; /* deepest stack byte touched */
+    std::vector<MapUse> map_use; /* per map index */
 };
 
 /* returns GX_OK or GX_E_VERIFY / GX_EINVAL; out.log explains a rejection */

@@ -17,6 +17,7 @@ struct JitProgram {
     std::vector<uint64_t> insns;
     std::vector<InsnInfo> info;
     std::vector<gx_map_spec> maps; /* layouts become compile-time constants */
+    std::vector<MapUse> use;       /* per map: may its updates be combined per block? */
     uint64_t budget = 1ull << 16;
 };
 
@@ -24,7 +25,32 @@ struct JitKernel {
     cudaKernel_t kernel = nullptr;
     std::string key;
     size_t smem_attr = 0;
+    uint32_t shard_bytes = 0; /* shared memory of the block-private combining area (max over programs) */
+    uint32_t wc_max_bits = 0; /* widest combining cache (0: no combinable map; 1: private arrays only) */
 };
+
+/* the block-private combining layout of one program (shared memory, 16-byte aligned pieces) */
+struct ShardMap {
+    int map = -1;
+    bool full = false;       /* whole private copy of an array map, else a tagged cache */
+    uint32_t tags_off = 0;   /* cache: 2^max_bits u64 tags */
+    uint32_t acc_off = 0;    /* accumulators: values laid out with the map's value stride */
+    uint32_t stride = 0;     /* value stride (bytes, multiple of 8) */
+    uint32_t max_bits = 0;   /* cache: log2 entries at most */
+    uint32_t n_values = 0;   /* full: max_entries */
+    std::vector<uint8_t> op; /* per 4-byte word of a value: UpdClass | UC_W8 */
+};
+struct ShardPlan {
+    std::vector<ShardMap> maps;
+    uint32_t bytes = 0;
+    uint32_t max_bits = 0;
+    const ShardMap *find(int m) const {
+        for (const ShardMap &s : maps)
+            if (s.map == m) return &s;
+        return nullptr;
+    }
+};
+ShardPlan plan_shards(const JitProgram &p);
 
 /* compile (or fetch from the caches) one kernel running progs[slot] for chunk slot `slot` */
 int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log);

@@ -124,8 +124,170 @@ int size_of(int op) { return (op & 0x18) == 0x00 ? 4 : (op & 0x18) == 0x08 ? 2 :
 
 std::string R(int r) { return "r" + std::to_string(r); }
 
+const uint32_t WC_FULL_MAX = 4096;  /* array maps up to this many bytes get a whole private copy */
+const uint32_t WC_CACHE_MAX = 8192; /* shared bytes of one map's cache (tags + accumulators) */
+const uint32_t WC_TOTAL_MAX = 24576; /* shared bytes of one program's combining area */
+const uint32_t WC_BITS = 8;         /* widest cache: 256 entries */
+
+uint32_t up16(uint32_t v) { return (v + 15u) & ~15u; }
+
+const char *uc_op(uint8_t c) {
+    switch (c & 0xF) {
+    case UC_ADD: return "AG_ADD";
+    case UC_OR: return "AG_OR";
+    case UC_AND: return "AG_AND";
+    case UC_XOR: return "AG_XOR";
+    case UC_MAX: return "AG_MAX";
+    default: return "AG_MIN";
+    }
+}
+
+/* bit j: word j of a value starts at all ones (AND / MIN identity) */
+uint64_t and_mask(const ShardMap &sm) {
+    uint64_t m = 0;
+    for (size_t j = 0; j < sm.op.size() && j < 64; j++)
+        if ((sm.op[j] & 0xF) == UC_AND || (sm.op[j] & 0xF) == UC_MIN) m |= 1ull << j;
+    return m;
+}
+
+/* the flush of one value's accumulators at shared `acc` (expression) into device memory at `gbase` */
+std::string flush_value(const ShardMap &sm, const std::string &acc, const std::string &gbase) {
+    std::ostringstream o;
+    for (uint32_t u = 0; u < sm.stride / 8; u++) {
+        uint8_t lo = 2 * u < sm.op.size() ? sm.op[2 * u] : 0, hi = 2 * u + 1 < sm.op.size() ? sm.op[2 * u + 1] : 0;
+        if (lo & UC_W8) {
+            o << "      wc_flush_word<" << uc_op(lo) << ", 8>((void *)(" << gbase << " + " << u * 8 << "), ((const u64 *)("
+              << acc << "))[" << u << "]);\n";
+            continue;
+        }
+        for (int h = 0; h < 2; h++) {
+            uint8_t c = h ? hi : lo;
+            if (!c) continue;
+            o << "      wc_flush_word<" << uc_op(c) << ", 4>((void *)(" << gbase << " + " << u * 8 + 4 * h
+              << "), (u64)((const u32 *)(" << acc << "))[" << 2 * u + h << "]);\n";
+        }
+    }
+    return o.str();
+}
+
+} // namespace
+
+ShardPlan plan_shards(const JitProgram &p) {
+    ShardPlan plan;
+    /* only maps that some update instruction reaches with a known offset are worth a shard */
+    std::vector<bool> targeted(p.maps.size(), false);
+    for (const InsnInfo &ii : p.info)
+        if (ii.visited && ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES && ii.vmap < (int)targeted.size())
+            targeted[ii.vmap] = true;
+    uint32_t off = 0;
+    for (size_t m = 0; m < p.maps.size() && m < p.use.size(); m++) {
+        const gx_map_spec &ms = p.maps[m];
+        if (!targeted[m] || !p.use[m].combinable()) continue;
+        if (ms.type != GX_MAP_ARRAY && ms.type != GX_MAP_HASH) continue;
+        ShardMap sm;
+        sm.map = (int)m;
+        sm.stride = (ms.value_size + 7u) & ~7u;
+        sm.op = p.use[m].op;
+        if (sm.stride > 256) continue; /* identities are kept as a 64-bit mask over a value's words */
+        uint64_t full_bytes = (uint64_t)ms.max_entries * sm.stride;
+        if (ms.type == GX_MAP_ARRAY && full_bytes <= WC_FULL_MAX) {
+            sm.full = true;
+            sm.n_values = ms.max_entries;
+            sm.acc_off = off;
+            uint32_t need = up16((uint32_t)full_bytes);
+            if (off + need > WC_TOTAL_MAX) continue;
+            off += need;
+        } else {
+            uint32_t bits = WC_BITS;
+            while (bits > 2 && (1u << bits) * (8u + sm.stride) > WC_CACHE_MAX) bits--;
+            uint32_t need = up16((1u << bits) * 8u) + up16((1u << bits) * sm.stride);
+            if (off + need > WC_TOTAL_MAX) continue;
+            sm.max_bits = bits;
+            sm.tags_off = off;
+            sm.acc_off = off + up16((1u << bits) * 8u);
+            off += need;
+            plan.max_bits = std::max(plan.max_bits, bits);
+        }
+        plan.maps.push_back(sm);
+    }
+    plan.bytes = off;
+    if (!plan.maps.empty() && plan.max_bits == 0) plan.max_bits = 1;
+    return plan;
+}
+
+namespace {
+
+/* block start: identities everywhere (every thread of the block calls this) */
+std::string gen_wc_init(const ShardPlan &sp, int slot) {
+    std::ostringstream o;
+    o << "__device__ __forceinline__ void gx_wc_init_" << slot << "(const ExecEnv &env) {\n";
+    for (const ShardMap &sm : sp.maps) {
+        const uint32_t wpv = sm.stride / 4;
+        if (sm.full) {
+            o << "  wc_fill(env.shard + " << sm.acc_off << ", " << sm.n_values * wpv << "u, " << wpv << "u, "
+              << hex64(and_mask(sm)) << ");\n";
+        } else {
+            o << "  { const u32 b_ = env.wc_bits < " << sm.max_bits << "u ? env.wc_bits : " << sm.max_bits << "u;\n"
+              << "    for (u32 i = threadIdx.x; i < (1u << b_); i += blockDim.x) ((u64 *)(env.shard + " << sm.tags_off
+              << "))[i] = 0;\n"
+              << "    wc_fill(env.shard + " << sm.acc_off << ", (1u << b_) * " << wpv << "u, " << wpv << "u, "
+              << hex64(and_mask(sm)) << "); }\n";
+        }
+    }
+    o << "}\n";
+    return o.str();
+}
+
+/* block end: add the block's totals into device memory (after a block barrier) */
+std::string gen_wc_flush(const ShardPlan &sp, int slot) {
+    std::ostringstream o;
+    o << "__device__ __forceinline__ void gx_wc_flush_" << slot << "(const ExecEnv &env) {\n";
+    for (const ShardMap &sm : sp.maps) {
+        const std::string vals = "env.maps[" + std::to_string(sm.map) + "].values";
+        if (sm.full) {
+            o << "  for (u32 v_ = threadIdx.x; v_ < " << sm.n_values << "u; v_ += blockDim.x) {\n"
+              << "    const uint8_t *a_ = env.shard + " << sm.acc_off << " + (size_t)v_ * " << sm.stride << ";\n"
+              << "    const u64 g_ = (u64)(" << vals << " + (size_t)v_ * " << sm.stride << ");\n"
+              << flush_value(sm, "a_", "g_") << "  }\n";
+        } else {
+            o << "  { const u32 b_ = env.wc_bits < " << sm.max_bits << "u ? env.wc_bits : " << sm.max_bits << "u;\n"
+              << "    for (u32 e_ = threadIdx.x; e_ < (1u << b_); e_ += blockDim.x) {\n"
+              << "      const u64 g_ = ((const u64 *)(env.shard + " << sm.tags_off << "))[e_];\n"
+              << "      if (!g_) continue;\n"
+              << "      const uint8_t *a_ = env.shard + " << sm.acc_off << " + (size_t)e_ * " << sm.stride << ";\n"
+              << flush_value(sm, "a_", "g_") << "    } }\n";
+        }
+    }
+    o << "}\n\n";
+    return o.str();
+}
+
+/* an update of map memory at `addr` by `val`: combined per block when the plan allows */
+std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, int size, const std::string &addr,
+                       const std::string &val) {
+    std::string global = std::string("agg_update<") + op + ", " + std::to_string(size) + ">(" + addr + ", " + val +
+                         ", __activemask());";
+    const ShardMap *sm = ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES ? sp.find(ii.vmap) : nullptr;
+    if (!sm) return global;
+    std::ostringstream o;
+    std::string t = std::string("<") + op + ", " + std::to_string(size) + ">";
+    o << "if (env.wc_bits) { const u64 a_ = " << addr << "; ";
+    if (sm->full) {
+        o << "sh_update" << t << "(sh_addr(env.shard + " << sm->acc_off << ") + (u32)(a_ - (u64)env.maps[" << sm->map
+          << "].values), " << val << "); ";
+    } else {
+        o << "const u32 b_ = env.wc_bits < " << sm->max_bits << "u ? env.wc_bits : " << sm->max_bits << "u; "
+          << "uint8_t *e_ = wc_entry(env.shard + " << sm->tags_off << ", env.shard + " << sm->acc_off << ", b_, "
+          << sm->stride << "u, a_ - " << ii.voff << "ull); "
+          << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); "
+          << "else plain_atomic" << t << "((void *)a_, " << val << "); ";
+    }
+    o << "} else " << global;
+    return o.str();
+}
+
 /* one program -> `__device__ u64 gx_body_<slot>(env, ctxw, valid, ev_idx)` */
-int gen_body(const JitProgram &p, int slot, std::string &out, std::string &log) {
+int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &out, std::string &log) {
     const uint32_t n = (uint32_t)p.insns.size();
     std::vector<uint8_t> target(n + 1, 0);
     for (uint32_t pc = 0; pc < n; pc++) {
@@ -251,10 +413,10 @@ int gen_body(const JitProgram &p, int slot, std::string &out, std::string &log) 
                     o << "((u32 *)(r1 - GX_RB_HDR))[1] = GX_RB_DISCARDED;";
                     break;
                 case GX_HELPER_ATOMIC_MAX_U64:
-                    o << "agg_update<AG_MAX, 8>(r1, r2, __activemask());";
+                    o << gen_update(sp, ii, "AG_MAX", 8, "r1", "r2");
                     break;
                 case GX_HELPER_ATOMIC_MIN_U64:
-                    o << "agg_update<AG_MIN, 8>(r1, r2, __activemask());";
+                    o << gen_update(sp, ii, "AG_MIN", 8, "r1", "r2");
                     break;
                 default: log = "jit: unknown helper"; return GX_EINVAL;
                 }
@@ -304,7 +466,8 @@ int gen_body(const JitProgram &p, int slot, std::string &out, std::string &log) 
                     int b = imm & ~1;
                     const char *ag = b == 0x00 ? "AG_ADD" : b == 0x40 ? "AG_OR" : b == 0x50 ? "AG_AND" : "AG_XOR";
                     if (imm & 1) o << R(src) << " = fetch_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ");";
-                    else o << "agg_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ", __activemask());";
+                    else if (ii.kind == MK_STACK) o << "agg_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ", __activemask());";
+                    else o << gen_update(sp, ii, ag, size, addr, R(src));
                 }
                 break;
             }
@@ -369,7 +532,24 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
     std::string src;
     src += "#include \"gx_device.cuh\"\nnamespace gx {\n";
     rc = GX_OK;
-    for (size_t i = 0; i < progs.size() && rc == GX_OK; i++) rc = gen_body(*progs[i], (int)i, src, log);
+    for (size_t i = 0; i < progs.size() && rc == GX_OK; i++) {
+        const ShardPlan sp = plan_shards(*progs[i]);
+        rc = gen_body(*progs[i], sp, (int)i, src, log);
+        src += gen_wc_init(sp, (int)i);
+        src += gen_wc_flush(sp, (int)i);
+    }
+    auto hook = [&](const char *what) {
+        std::string h = std::string("  [](const gx::ExecEnv &env) {\n");
+        if (progs.size() == 1) {
+            h += std::string("    gx::gx_wc_") + what + "_0(env);\n";
+        } else {
+            h += "    switch (env.slot) {\n";
+            for (size_t i = 0; i < progs.size(); i++)
+                h += "    case " + std::to_string(i) + ": gx::gx_wc_" + what + "_" + std::to_string(i) + "(env); break;\n";
+            h += "    }\n";
+        }
+        return h + "  }";
+    };
     src += "} // namespace gx\n\nextern \"C\" __global__ void __launch_bounds__(256) gx_jit_kernel(gx::ExecParams P) {\n"
            "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx::u64 *ctxw, bool valid, gx::u64 ev_idx) -> gx::u64 {\n";
     if (progs.size() == 1) {
@@ -381,7 +561,7 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
                    "(env, ctxw, valid, ev_idx);\n";
         src += "    }\n    return 0;\n";
     }
-    src += "  });\n}\n";
+    src += "  },\n" + hook("init") + ",\n" + hook("flush") + ");\n}\n";
     return src;
 }
 
@@ -433,6 +613,13 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
     int rc;
     const std::string src = jit_source(progs, log, rc);
     if (rc) return rc;
+    out.shard_bytes = 0;
+    out.wc_max_bits = 0;
+    for (const JitProgram *p : progs) {
+        const ShardPlan sp = plan_shards(*p);
+        out.shard_bytes = std::max(out.shard_bytes, sp.bytes);
+        out.wc_max_bits = std::max(out.wc_max_bits, sp.max_bits);
+    }
     const std::string key = jit_key(src);
     {
         std::lock_guard<std::mutex> g(cache_mu);
@@ -492,6 +679,7 @@ extern "C" int gx_jit_check(const uint64_t *insns, uint32_t n, const gx_map_spec
         jp.insns.assign(insns, insns + n);
         jp.info = v.info;
         jp.maps.assign(maps, maps + n_maps);
+        jp.use = v.map_use;
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
         const std::string src = gx::jit_source({&jp}, msg, rc);
         std::vector<char> cubin;

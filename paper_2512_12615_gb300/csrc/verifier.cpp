@@ -635,6 +635,42 @@ struct Verifier {
         return GX_OK;
     }
 
+    /* ---------------------------------------------------- map-value use (block-private combining) */
+    void use_other(int m) {
+        if (m >= 0 && m < (int)out->map_use.size()) out->map_use[m].other = true;
+    }
+
+    /* where an update lands: the map and constant value offset, merged over every path */
+    void note_vmap(u32 pc, int m, int voff) {
+        InsnInfo &ii = out->info[pc];
+        int16_t vo = voff >= 0 ? (int16_t)voff : InsnInfo::ARG_VARIES;
+        if (ii.vmap == -1) {
+            ii.vmap = (int8_t)m;
+            ii.voff = vo;
+        } else if (ii.vmap != (int8_t)m) {
+            ii.vmap = -2;
+        } else if (ii.voff != vo) {
+            ii.voff = InsnInfo::ARG_VARIES;
+        }
+    }
+
+    /* a non-fetching commutative update of `size` bytes at p + off (p a map-value pointer) */
+    void use_update(u32 pc, const Reg &p, int off, int size, int cls) {
+        MapUse &u = out->map_use[p.map];
+        if (!is_const(p)) {
+            u.other = true;
+            note_vmap(pc, p.map, -1);
+            return;
+        }
+        int lo = (int)p.smin + off;
+        note_vmap(pc, p.map, lo);
+        uint8_t code = (uint8_t)(cls | (size == 8 ? UC_W8 : 0));
+        for (int w = lo / 4; w < (lo + size) / 4; w++) {
+            if (u.op[w] == UC_NONE) u.op[w] = code;
+            else if (u.op[w] != code) u.mixed = true;
+        }
+    }
+
     /* ---------------------------------------------------- memory checks */
     int note(u32 pc, uint8_t kind, int off) {
         InsnInfo &ii = out->info[pc];
@@ -749,6 +785,7 @@ struct Verifier {
             if (!is_const(p) ? p.tz < need : (p.smin & ((1 << need) - 1)))
                 return fail(pc, "%s: pointer misaligned", what);
             if (p.t == MV && opts.deterministic && tainted) *tainted = true;
+            if (p.t == MV) use_other(p.map); /* a helper reads these bytes */
             return GX_OK;
         }
         return fail(pc, "%s: expected a stack or map-value pointer, got %s", what, rt_name(p.t));
@@ -1152,6 +1189,7 @@ struct Verifier {
             case MV:
                 if (check_range(pc, p, off, size, maps[p.map].value_size, "map value")) return GX_E_VERIFY;
                 v.taint = det ? 1 : 0;
+                use_other(p.map);
                 if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
                 break;
             case RB:
@@ -1193,6 +1231,7 @@ struct Verifier {
             case MV:
                 if (check_range(pc, p, off, size, maps[p.map].value_size, "map value")) return GX_E_VERIFY;
                 if (det) return fail(pc, "plain store into map memory in deterministic mode");
+                use_other(p.map);
                 if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
                 break;
             case RB:
@@ -1233,6 +1272,13 @@ struct Verifier {
                 int cls = base == 0x00 ? OPC_ADD : base == 0x40 ? OPC_OR : base == 0x50 ? OPC_AND : OPC_XOR;
                 if (note_update(pc, p, off, size, cls)) return GX_E_VERIFY;
             }
+            if (xchg || cmpx || fetch) {
+                use_other(p.map);
+                note_vmap(pc, -2, -1);
+            } else {
+                int uc = base == 0x00 ? UC_ADD : base == 0x40 ? UC_OR : base == 0x50 ? UC_AND : UC_XOR;
+                use_update(pc, p, off, size, uc);
+            }
             if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
         } else if (p.t == STK) {
             int abs = 0;
@@ -1242,6 +1288,7 @@ struct Verifier {
             old.taint = cur.taint;
             bool t = cur.taint || s.r[src].taint || (cmpx && s.r[0].taint);
             stack_write(s, abs, size, nullptr, t);
+            note_vmap(pc, -2, -1);
             if (note(pc, MK_STACK, abs)) return GX_E_VERIFY;
         } else {
             return fail(pc, "atomic on a %s", rt_name(p.t));
@@ -1302,6 +1349,7 @@ struct Verifier {
             if (mem_arg(pc, s, s.r[2], m.key_size, "update key", &tk, &kc)) return GX_E_VERIFY;
             if (mem_arg(pc, s, s.r[3], m.value_size, "update value", &tv, &vc)) return GX_E_VERIFY;
             if (s.r[4].t != SC) return fail(pc, "update flags must be a scalar");
+            if (!is_const(s.r[4]) || s.r[4].umin != GX_NOEXIST) use_other(s.r[1].map); /* may overwrite a value */
             if (det) {
                 if (tk) return fail(pc, "order-dependent map key");
                 if (!is_const(s.r[4]) || s.r[4].umin != GX_NOEXIST)
@@ -1367,6 +1415,7 @@ struct Verifier {
             if (s.r[2].t != SC) return fail(pc, "atomic max/min operand must be a scalar");
             if (det && s.r[2].taint) return fail(pc, "order-dependent value folded into map memory");
             if (note_update(pc, p, 0, 8, id == GX_HELPER_ATOMIC_MAX_U64 ? OPC_MAX : OPC_MIN)) return GX_E_VERIFY;
+            use_update(pc, p, 0, 8, id == GX_HELPER_ATOMIC_MAX_U64 ? UC_MAX : UC_MIN);
             r0_void = true;
             if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
             break;
@@ -1381,6 +1430,8 @@ struct Verifier {
     /* ---------------------------------------------------- driver */
     int run() {
         out->info.assign(n, InsnInfo());
+        out->map_use.assign(n_maps, MapUse());
+        for (u32 m = 0; m < n_maps && m < GX_MAX_MAPS; m++) out->map_use[m].op.assign((maps[m].value_size + 3) / 4, UC_NONE);
         if (n == 0 || n > GX_MAX_INSNS) return fail(0, "program length %u not in [1, %d]", n, GX_MAX_INSNS);
         if (opts.ctx_size < 8 || opts.ctx_size > GX_MAX_CTX || opts.ctx_size % 8)
             return fail(0, "ctx_size %u invalid", opts.ctx_size);

@@ -36,7 +36,21 @@ class ProgOpts(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("block", u32), ("ept", u32), ("grid", u32), ("reserved", u32)]
+    _fields_ = [("block", u32), ("ept", u32), ("grid", u32), ("shards", u32)]
+
+
+class Analysis(ctypes.Structure):
+    _fields_ = [("insns_processed", u64), ("stack_depth", u32), ("combinable_maps", u32)]
+
+
+SHARDS_OFF = 255
+
+
+def _launch(launch) -> Optional[Launch]:
+    """(block, ept) or (block, ept, shards) -> gx_launch; 0 fields mean tuned/default."""
+    if launch is None:
+        return None
+    return Launch(launch[0], launch[1], 0, launch[2] if len(launch) > 2 else 0)
 
 
 class RunStats(ctypes.Structure):
@@ -75,6 +89,8 @@ _SIGS = {
                                ctypes.c_void_p]),
     "gx_verify": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                         ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_analyze": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                         ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "gx_jit_check": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                            ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
@@ -171,6 +187,20 @@ def verify(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, determin
     log = ctypes.create_string_buffer(1024)
     rc = lib().gx_verify(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), log, 1024)
     return rc, log.value.decode()
+
+
+def analyze(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, deterministic: bool = False,
+            insn_budget: int = 0) -> Tuple[int, Analysis, str]:
+    """Host-only verification plus what it proved: (status, gx_analysis, log)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    specs = (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"])
+                                                   for s in map_specs])
+    opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
+    out = Analysis()
+    log = ctypes.create_string_buffer(1024)
+    rc = lib().gx_analyze(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
+                          ctypes.byref(out), log, 1024)
+    return rc, out, log.value.decode()
 
 
 PROG_JIT = 1
@@ -284,10 +314,10 @@ class Program:
         return lib().gx_prog_uops(self.h)
 
     def run(self, events, n: Optional[int] = None, *, ret_out=None, idx_base: int = 0,
-            launch: Optional[Tuple[int, int]] = None, stream=None) -> None:
+            launch: Optional[Tuple[int, ...]] = None, stream=None) -> None:
         if n is None:
             n = events.numel() * events.element_size() // self.ctx_size
-        lp = None if launch is None else ctypes.byref(Launch(launch[0], launch[1], 0, 0))
+        lp = None if launch is None else ctypes.byref(_launch(launch))
         check(lib().gx_run_batch_ex(self.h, _ptr(events), n, idx_base, _ptr(ret_out), lp, _stream(stream)),
               "gx_run_batch_ex")
 
@@ -301,12 +331,13 @@ class Program:
         check(lib().gx_last_status(self.h, ctypes.byref(st), int(reset), _stream(stream)), "gx_last_status")
         return st
 
-    def autotune(self, events, n: Optional[int] = None, stream=None) -> Tuple[int, int]:
+    def autotune(self, events, n: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
+        """Returns the chosen (block, ept, shards)."""
         if n is None:
             n = events.numel() * events.element_size() // self.ctx_size
         best = Launch()
         check(lib().gx_autotune(self.h, _ptr(events), n, _stream(stream), ctypes.byref(best)), "gx_autotune")
-        return best.block, best.ept
+        return best.block, best.ept, best.shards
 
 
 class Batch:
@@ -318,8 +349,8 @@ class Batch:
     def add(self, prog: Program, events, n: int, ret_out=None) -> None:
         check(lib().gx_batch_add(self.h, prog.h, _ptr(events), n, _ptr(ret_out)), "gx_batch_add")
 
-    def plan(self, launch: Optional[Tuple[int, int]] = None, stream=None) -> None:
-        lp = None if launch is None else ctypes.byref(Launch(launch[0], launch[1], 0, 0))
+    def plan(self, launch: Optional[Tuple[int, ...]] = None, stream=None) -> None:
+        lp = None if launch is None else ctypes.byref(_launch(launch))
         check(lib().gx_batch_plan(self.h, lp, _stream(stream)), "gx_batch_plan")
 
     def launch(self, stream=None) -> None:

@@ -76,15 +76,25 @@ def assert_same(gpu_snap, ora_snap) -> None:
 
 
 def run_both(ctx: gx.Context, prog: np.ndarray, specs: Sequence[dict], ctx_size: int, events: np.ndarray, *,
-             det: bool = True, launch: Optional[Tuple[int, int]] = None, idx_base: int = 0, check_r0: bool = True,
-             jit: bool = False):
-    """Returns (gpu snapshot, oracle snapshot, r0 gpu, r0 oracle) after asserting equality."""
+             det: bool = True, launch: Optional[Tuple[int, ...]] = None, idx_base: int = 0, check_r0: bool = True,
+             jit: bool = False, init: Optional[Sequence[Optional[bytes]]] = None):
+    """Returns (gpu snapshot, oracle snapshot, r0 gpu, r0 oracle) after asserting equality.
+
+    init: per map, None or the initial values of an array map (max_entries * value_size bytes)."""
     import torch
 
     n = np.ascontiguousarray(events).view(np.uint8).size // ctx_size
     om = O.maps_from_specs(specs)
+    for i, blob in enumerate(init or []):
+        if blob is not None:
+            vs = specs[i]["value_size"]
+            for k in range(specs[i]["max_entries"]):
+                assert om[i].update(k.to_bytes(4, "little"), blob[k * vs:(k + 1) * vs]) == 0
     r0_o, _ = O.run(prog, om, events, ctx_size, want_r0=True, event_idx_base=idx_base)
     gm = gpu_maps(ctx, specs)
+    for i, blob in enumerate(init or []):
+        if blob is not None:
+            gm[i].write(blob)
     p = gx.Program(ctx, prog, gm, ctx_size, deterministic=det, jit=jit)
     dev = device_events(events)
     ret = torch.zeros(max(n, 1), dtype=torch.int64, device="cuda")
