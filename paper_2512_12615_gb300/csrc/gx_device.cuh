@@ -398,6 +398,28 @@ __device__ int hash_delete(const gx_dmap &m, const uint8_t *k, u64 *stats) {
     return GX_ENOENT;
 }
 
+/*
+ * Per-lane lookup of a key of KS <= 8 bytes (KS in 1, 2, 4, 8), given as its zero-padded
+ * little-endian word, in a hash map whose slots are 16 bytes and values VS bytes apart:
+ * the form specialised programs inline.  No warp collectives.
+ */
+template <int KS, int VS>
+__device__ __forceinline__ u64 hash_find_word(const gx_dmap &m, u64 kw, u64 *stats) {
+    const u64 mask = m.mask;
+    u64 i = mix64(0x9E3779B97F4A7C15ull ^ (u64)KS ^ kw) & mask;
+    for (u64 probes = 0; probes <= mask; probes++, i = (i + 1) & mask) {
+        const uint8_t *slot = m.slots + i * 16u;
+        u32 s = ld_acquire((const u32 *)slot);
+        if (s == GX_SLOT_EMPTY) return 0;
+        if (s == GX_SLOT_BUSY) {
+            s = wait_published((u32 *)slot, stats);
+            if (s == GX_SLOT_BUSY) return 0;
+        }
+        if (s == GX_SLOT_FULL && *(const u64 *)(slot + 8) == kw) return (u64)(m.values + i * (u64)VS);
+    }
+    return 0;
+}
+
 /* lookup with lanes that look up the same (<= 8 byte) key sharing one probe */
 __device__ __noinline__ u64 map_lookup(const gx_dmap &m, const uint8_t *k, u32 exec, u64 *stats) {
     if (m.type == GX_MAP_ARRAY) {

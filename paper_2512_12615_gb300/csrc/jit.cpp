@@ -388,9 +388,25 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             if (code == 0x80) {
                 std::string m = ii.map >= 0 ? "env.maps[" + std::to_string(ii.map) + "]" : "env.maps[r1]";
                 switch (imm) {
-                case GX_HELPER_MAP_LOOKUP:
-                    o << "r0 = map_lookup(" << m << ", (const uint8_t *)r2, __activemask(), env.stats);";
+                case GX_HELPER_MAP_LOOKUP: {
+                    /* one map and a key at a known stack slot: inline, per lane, layout as constants */
+                    const gx_map_spec *ms = ii.map >= 0 && ii.map < (int)p.maps.size() ? &p.maps[ii.map] : nullptr;
+                    const bool key_known = ii.a2 < 0 && ii.a2 >= -GX_STACK_BYTES;
+                    const uint32_t vs = ms ? (ms->value_size + 7u) & ~7u : 0;
+                    const std::string key = "(const uint8_t *)stack + " + std::to_string(ii.a2 + GX_STACK_BYTES);
+                    if (ms && key_known && ms->type == GX_MAP_ARRAY) {
+                        o << "{ const u32 k_ = (u32)load_sz<4, false>(" << key << "); r0 = k_ < " << ms->max_entries
+                          << "u ? (u64)(" << m << ".values + (u64)k_ * " << vs << "u) : 0ull; }";
+                    } else if (ms && key_known && ms->type == GX_MAP_HASH &&
+                               (ms->key_size == 1 || ms->key_size == 2 || ms->key_size == 4 || ms->key_size == 8)) {
+                        const std::string ks = std::to_string(ms->key_size);
+                        o << "r0 = hash_find_word<" << ks << ", " << vs << ">(" << m << ", load_sz<" << ks << ", false>("
+                          << key << "), env.stats);";
+                    } else {
+                        o << "r0 = map_lookup(" << m << ", (const uint8_t *)r2, __activemask(), env.stats);";
+                    }
                     break;
+                }
                 case GX_HELPER_MAP_UPDATE:
                     o << "r0 = (u64)(s64)map_update(" << m
                       << ", (const uint8_t *)r2, (const uint8_t *)r3, r4, __activemask(), env.stats);";
