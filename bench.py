@@ -255,31 +255,33 @@ def run_counting(gx, torch, jit=True):
     return out
 
 
-def run_latency(gx, torch, jit=True):
+def run_latency(gx, torch, jit=True, pairs=None):
+    pairs = pairs or C3_PAIRS
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
     prog_i, specs, cs = P.latency()
-    ev = gen.latency_pairs(C3_PAIRS, seed=SEED)
+    ev = gen.latency_pairs(pairs, seed=SEED)
     dev = to_device(ev)
     del ev
     ctx = gx.Context(torch.cuda.current_device())
     maps = [gx.Map.from_spec(ctx, s) for s in specs]
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
-    prog.autotune(dev, C3_PAIRS, stream=sid)
+    prog.autotune(dev, pairs, stream=sid)
     times = []
     for r in range(8):
         t = EventTimer(stream)
         with t:
-            prog.run(dev, C3_PAIRS, stream=sid)
+            prog.run(dev, pairs, stream=sid)
         ms = t.ms()
         raw, dropped = maps[1].drain(stream=sid)
         if r >= 2:
             times.append(ms)
     ms = float(np.median(times))
-    nbytes = C3_PAIRS * 64 + len(raw)
+    nbytes = pairs * 64 + len(raw)
     peak, _ = peaks()
-    out = {"workload": "latency 256M records (128M entry/exit pairs), 4096x64 histogram, 1% outliers to ringbuf",
-           "Mevents_per_s": round(2 * C3_PAIRS / ms / 1e3, 1), "Mpairs_per_s": round(C3_PAIRS / ms / 1e3, 1),
+    out = {"workload": f"latency {2 * pairs} records ({pairs} entry/exit pairs), 4096x64 histogram, 1% outliers "
+                       "to ringbuf",
+           "Mevents_per_s": round(2 * pairs / ms / 1e3, 1), "Mpairs_per_s": round(pairs / ms / 1e3, 1),
            "kernel_ms_median": round(ms, 4), "GBps": round(nbytes / ms / 1e6, 1),
            "hbm_frac": round(nbytes / ms / 1e6 / peak, 4), "ringbuf_bytes": len(raw), "dropped": dropped}
     prog.destroy()
@@ -307,6 +309,12 @@ def run_batched(gx, torch):
     ctx = gx.Context(torch.cuda.current_device())
     items = build_batch(gx, torch, ctx, sizes)
     total = sum(sizes)
+    # planning tunes each program's map sharding (and the batch's launch shape) on scratch maps; the
+    # plain launches below use the same per-program choices
+    b = gx.Batch(ctx)
+    for prog, _, dev, n in items:
+        b.add(prog, dev, n)
+    b.plan(stream=sid)
     # plain: 64 launches
     for _ in range(2):
         for prog, _, dev, n in items:
@@ -318,10 +326,6 @@ def run_batched(gx, torch):
             for prog, _, dev, n in items:
                 prog.run(dev, n, stream=sid)
         tp.append(t.ms())
-    b = gx.Batch(ctx)
-    for prog, _, dev, n in items:
-        b.add(prog, dev, n)
-    b.plan(stream=sid)
     for _ in range(2):
         b.launch(stream=sid)
     tb = []
@@ -344,7 +348,7 @@ def run_batched(gx, torch):
     return out
 
 
-def run_served(gx, torch, seconds: float):
+def run_served(gx, torch, seconds: float, lam: float = 20000.0):
     ctx = gx.Context(torch.cuda.current_device())
     rng = np.random.default_rng(SEED)
     progs = P.batch_programs()
@@ -352,7 +356,6 @@ def run_served(gx, torch, seconds: float):
     for prog_i, specs, cs in progs:
         maps = [gx.Map.from_spec(ctx, s) for s in specs]
         loaded.append((gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=True), maps))
-    lam = 20000.0
     n_req = int(lam * seconds)
     gaps = rng.exponential(1.0 / lam, n_req)
     offs = np.cumsum(gaps)
@@ -459,7 +462,10 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "headline"])
+    ap.add_argument("--only", default="all", choices=["all", "headline", "latency", "batched", "served"],
+                    help="all / the headline line only / one config alone (for profiling)")
+    ap.add_argument("--pairs", type=int, default=C3_PAIRS, help="latency pairs with --only latency")
+    ap.add_argument("--serve-rate", type=float, default=20000.0, help="served config arrival rate (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -480,6 +486,12 @@ def main() -> int:
     import paper_2512_12615_gb300 as gx
 
     gx.lib()
+    if args.only in ("latency", "batched", "served"):
+        one = {"latency": lambda: run_latency(gx, torch, True, args.pairs), "batched": lambda: run_batched(gx, torch),
+               "served": lambda: run_served(gx, torch, args.serve_seconds, args.serve_rate)}[args.only]()
+        if rank == 0:
+            print(json.dumps({"config": args.only, **one}), flush=True)
+        return 0
     head = run_headline(args, gx, torch, (rank, world), jit=True)
     configs = {}
     if rank == 0:
@@ -496,7 +508,8 @@ def main() -> int:
                          ("latency_256M", lambda: run_latency(gx, torch, True)),
                          ("latency_256M_interpreter", lambda: run_latency(gx, torch, False)),
                          ("batched_64_programs", lambda: run_batched(gx, torch)),
-                         ("served_poisson", lambda: run_served(gx, torch, args.serve_seconds))):
+                         ("served_poisson", lambda: run_served(gx, torch, args.serve_seconds, args.serve_rate)),
+                         ("served_poisson_2k", lambda: run_served(gx, torch, args.serve_seconds, 2000.0))):
             try:
                 configs[name] = fn()
             except Exception as e:  # a failing extra must not hide the headline

@@ -129,9 +129,13 @@ const char *gx_strerror(int status);
  *   GX_MAP_RINGBUF: key_size = value_size = 0; max_entries = buffer bytes (power of two,
  *                   >= 4096).  Records are {u32 len; u32 flags; u64 event_idx} + payload
  *                   padded to 8 bytes; the buffer fills from offset 0 until drained.
- * flags: reserved, must be 0.
+ * flags: 0, or GX_MAP_F_NO_DELETE for a hash map whose keys are never removed: the
+ *   verifier rejects map_delete_elem on it (gx_map_clear still empties it).  A published
+ *   slot of such a map never changes, so specialised programs may read slots through
+ *   the L1 cache; hot keys then stop converging on one L2 slice.
  * Memory is taken from the context budget (GX_ENOMEM when exceeded).
  */
+#define GX_MAP_F_NO_DELETE 1u
 int gx_map_create(gx_ctx *ctx, uint32_t type, uint32_t key_size, uint32_t value_size, uint32_t max_entries,
                   uint32_t flags, gx_map **out);
 /* Drop the caller's reference; the map is freed once no program references it. */
@@ -190,6 +194,8 @@ int gx_ringbuf_drain(gx_map *rb, void *host_out, uint64_t cap, uint64_t *bytes_o
 /* ---------------------------------------------------------------- programs (Sec. 4.4, Sec. 5.3) */
 typedef struct gx_map_spec {
     uint32_t type, key_size, value_size, max_entries;
+    uint32_t flags;    /* GX_MAP_F_* as given to gx_map_create */
+    uint32_t reserved; /* 0 */
 } gx_map_spec;
 
 typedef struct gx_prog_opts {
@@ -256,9 +262,13 @@ typedef struct gx_launch {
                         combinable maps (gx_analyze) are first combined in shared memory per block,
                         small array maps whole, other maps in a cache of 2^shards entries (2..10, capped
                         per map by its value size); GX_SHARDS_OFF sends every update to device memory
-                        (warp-aggregated); 0 = tuned/default.  Ignored by the interpreter. */
+                        (warp-aggregated); 0 = tuned/default.  OR GX_SHARDS_AGG into a width (or into 0
+                        for the default width) to warp-aggregate the updates that miss the cache, which
+                        pays when hot values miss and costs a warp match on every miss.  Ignored by the
+                        interpreter. */
 } gx_launch;
 #define GX_SHARDS_OFF 255u
+#define GX_SHARDS_AGG 0x100u
 
 /*
  * Run the program once per event over n records at events_dev (n * ctx_size bytes,

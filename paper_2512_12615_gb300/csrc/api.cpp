@@ -83,6 +83,20 @@ std::vector<uint8_t> build_image(const gx_prog *p, const std::vector<gx_dmap> &d
     return img;
 }
 
+/* gx_launch.shards: OFF, or a width in 2..10 (0 = default) with an optional GX_SHARDS_AGG */
+bool shards_valid(uint32_t sh) {
+    if (sh == GX_SHARDS_OFF) return true;
+    if (sh & ~(GX_SHARDS_AGG | 0xFFu)) return false;
+    uint32_t w = sh & 0xFFu;
+    return w == 0 || (w >= 2 && w <= 10);
+}
+
+/* ExecParams.wc_bits of a validated, enabled gx_launch.shards */
+uint32_t shards_param(uint32_t sh, uint32_t default_bits) {
+    uint32_t w = sh & 0xFFu;
+    return (w ? w : default_bits) | ((sh & GX_SHARDS_AGG) ? 0x100u : 0u);
+}
+
 /* dynamic shared memory of one block: staged image(s) + transposed ctx tiles */
 uint64_t exec_smem(uint32_t image_area, uint32_t block, uint32_t ctx_size) {
     return (uint64_t)image_area + (block / 32) * (uint64_t)(ctx_size / 8) * 256;
@@ -108,9 +122,10 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     uint32_t area = (uint32_t)round_up(image_bytes, 16);
     uint64_t smem = exec_smem(area, block, p->opts.ctx_size);
     uint32_t wc = 0, shard_off = 0;
-    if (lp.shards && lp.shards != GX_SHARDS_OFF && (lp.shards < 2 || lp.shards > 10)) return GX_EINVAL;
-    if (p->jit && p->jk.shard_bytes && lp.shards != GX_SHARDS_OFF) {
-        wc = lp.shards ? lp.shards : p->jk.wc_max_bits;
+    if (!shards_valid(lp.shards)) return GX_EINVAL;
+    const uint32_t sh = (lp.shards == 0 && p->pref_tuned) ? p->pref_shards : lp.shards; /* the program's tuned choice */
+    if (p->jit && p->jk.shard_bytes && sh != GX_SHARDS_OFF) {
+        wc = shards_param(sh, p->jk.wc_max_bits);
         shard_off = (uint32_t)round_up(smem, 16);
         smem = shard_off + p->jk.shard_bytes;
     }
@@ -222,9 +237,9 @@ uint64_t gx_mem_used(const gx_ctx *c) { return c ? c->used : 0; }
 /* ---------------------------------------------------------------- maps */
 int gx_map_create(gx_ctx *c, uint32_t type, uint32_t key_size, uint32_t value_size, uint32_t max_entries,
                   uint32_t flags, gx_map **out) {
-    if (!c || !out || flags) return GX_EINVAL;
+    if (!c || !out || (flags & ~GX_MAP_F_NO_DELETE) || (flags && type != GX_MAP_HASH)) return GX_EINVAL;
     *out = nullptr;
-    gx_map_spec spec = {type, key_size, value_size, max_entries};
+    gx_map_spec spec = {type, key_size, value_size, max_entries, flags, 0};
     gx_dmap d;
     memset(&d, 0, sizeof d);
     d.type = type;
@@ -644,10 +659,9 @@ int gx_last_status(gx_prog *p, gx_run_stats *out, int reset, void *stream) {
     return GX_OK;
 }
 
-int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_launch *best) {
+static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_t s, gx_launch *best, bool policy_only) {
     if (!p || (!events && n)) return GX_EINVAL;
     if (n == 0) return GX_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
     gx_ctx *c = p->ctx;
     /* scratch copies of every map, so tuning runs leave the real maps untouched */
     std::vector<void *> clones;
@@ -689,9 +703,11 @@ int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_lau
     gx_launch chosen;
     tuned_launch(p, n, &chosen);
     if (rc == GX_OK) {
-        const uint64_t sample = std::min<uint64_t>(n, 1ull << 24);
-        const uint32_t blocks[] = {128, 256};
-        const uint32_t epts[] = {1, 2, 4, 8, 16, 32, 64};
+        /* policy only: the sharding choice at one shape on a smaller sample (batch planning) */
+        const uint64_t sample = std::min<uint64_t>(n, policy_only ? (1ull << 21) : (1ull << 24));
+        const std::vector<uint32_t> blocks = policy_only ? std::vector<uint32_t>{256} : std::vector<uint32_t>{128, 256};
+        const std::vector<uint32_t> epts =
+            policy_only ? std::vector<uint32_t>{8} : std::vector<uint32_t>{1, 2, 4, 8, 16, 32, 64};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -701,7 +717,7 @@ int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_lau
         std::vector<uint32_t> widths = {0};
         if (p->jit && p->jk.shard_bytes) {
             widths = {GX_SHARDS_OFF, 0};
-            if (p->jk.wc_max_bits > 6) widths.push_back(6);
+            if (p->jk.wc_max_bits > 1) widths.push_back(GX_SHARDS_AGG); /* programs with a cache */
         }
         for (uint32_t b : blocks) {
             for (uint32_t e : epts) for (uint32_t w : widths) {
@@ -722,8 +738,9 @@ int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_lau
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         p->launches -= 0; /* tuning launches are counted like any other */
-        int bucket = 63 - __builtin_clzll(n | 1);
-        p->tuned[bucket] = chosen;
+        if (!policy_only) p->tuned[63 - __builtin_clzll(n | 1)] = chosen;
+        p->pref_shards = chosen.shards;
+        p->pref_tuned = true;
         if (cudaGetLastError() != cudaSuccess) rc = GX_E_CUDA;
     }
     cudaStreamSynchronize(s);
@@ -733,4 +750,19 @@ int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_lau
     return rc;
 }
 
+int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_launch *best) {
+    return autotune_impl(p, events, n, (cudaStream_t)stream, best, false);
+}
+
 } /* extern "C" */
+
+namespace gx {
+int tune_shards(gx_prog *p, const void *events, uint64_t n, cudaStream_t s) {
+    if (!p->jit || !p->jk.shard_bytes) {
+        p->pref_tuned = true;
+        p->pref_shards = 0;
+        return GX_OK;
+    }
+    return autotune_impl(p, events, n, s, nullptr, true);
+}
+} // namespace gx

@@ -48,9 +48,14 @@ struct Item {
     int64_t *ret_out;
 };
 
-/* cut items into chunks of `chunk_events`, largest item first; slots: program -> slot of a multi-program kernel */
+/*
+ * Cut items into chunks of `chunk_events`, largest item first; slots: program -> slot of a
+ * multi-program kernel.  With `pref_bits` set (the kernel's widest combining cache), a chunk
+ * of a program whose sharding was tuned carries that choice (bit 63 of pad, the
+ * ExecParams.wc_bits value in bits 32..40).
+ */
 void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vector<gx_chunk> &out,
-                 const std::map<gx_prog *, uint32_t> *slots = nullptr) {
+                 const std::map<gx_prog *, uint32_t> *slots = nullptr, uint32_t pref_bits = 0) {
     std::vector<size_t> order(items.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return items[a].n > items[b].n; });
@@ -69,6 +74,11 @@ void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vec
             c.image_bytes = it.prog->image_bytes;
             c.ctx_size = it.prog->opts.ctx_size;
             c.pad = slots ? slots->at(it.prog) : 0;
+            if (pref_bits && it.prog->pref_tuned && it.prog->pref_shards) {
+                uint32_t sh = it.prog->pref_shards;
+                uint32_t wc = sh == GX_SHARDS_OFF ? 0u : shards_param(sh, pref_bits);
+                c.pad |= (1ull << 63) | ((uint64_t)wc << 32);
+            }
             out.push_back(c);
         }
     }
@@ -110,8 +120,8 @@ struct Persist {
         max_ctx = ctx_max;
         smem = exec_smem(area, block, max_ctx);
         uint32_t wc = 0, shard_off = 0;
-        if (jk && jk->shard_bytes && shards != GX_SHARDS_OFF) {
-            wc = shards ? shards : jk->wc_max_bits;
+        if (jk && jk->shard_bytes) { /* chunks may switch combining on even when the default is off */
+            wc = shards == GX_SHARDS_OFF ? 0u : shards_param(shards, jk->wc_max_bits);
             shard_off = (uint32_t)round_up(smem, 16);
             smem = shard_off + jk->shard_bytes;
         }
@@ -258,7 +268,9 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t 
         area = std::max(area, it.prog->image_bytes);
         max_ctx = std::max(max_ctx, it.prog->opts.ctx_size);
     }
-    make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr);
+    /* the default width lets every program use its own tuned sharding */
+    const uint32_t pref = (b->jit && shards == 0) ? b->jk.wc_max_bits : 0;
+    make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr, pref);
     b->persist.jk = b->jit ? &b->jk : nullptr;
     int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size(), shards);
     if (rc) return rc;
@@ -280,7 +292,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
     if (lp) {
         uint32_t blk = lp->block ? lp->block : 256, ept = lp->ept ? lp->ept : 4;
         if (blk < 64 || blk > GX_MAX_BLOCK || blk % 32 || ept < 1 || ept > 64) return GX_EINVAL;
-        if (lp->shards && lp->shards != GX_SHARDS_OFF && (lp->shards < 2 || lp->shards > 10)) return GX_EINVAL;
+        if (!shards_valid(lp->shards)) return GX_EINVAL;
         int rc = batch_plan_shape(b, blk, ept, lp->shards);
         if (rc == GX_OK) b->planned = true;
         return rc;
@@ -295,6 +307,15 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
             if (std::find(maps.begin(), maps.end(), m) == maps.end()) maps.push_back(m);
     std::vector<void *> saved(maps.size(), nullptr);
     int rc = GX_OK;
+    /* each program's own sharding first (on its largest item, scratch maps) */
+    if (b->jit) {
+        std::map<gx_prog *, const Item *> largest;
+        for (auto &it : b->items)
+            if (!largest.count(it.prog) || largest[it.prog]->n < it.n) largest[it.prog] = &it;
+        for (auto &kv : largest)
+            if (!kv.first->pref_tuned && kv.second->n && rc == GX_OK)
+                rc = gx::tune_shards(kv.first, kv.second->events, kv.second->n, s);
+    }
     for (size_t i = 0; i < maps.size() && rc == GX_OK; i++) {
         rc = dalloc(b->ctx, maps[i]->dbytes, &saved[i]);
         if (rc == GX_OK &&
@@ -309,8 +330,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
         cudaEventCreate(&e1);
         const uint32_t blocks[] = {128, 256};
         const uint32_t epts[] = {2, 4, 8, 16};
-        std::vector<uint32_t> widths = {0};
-        if (b->jit && b->jk.shard_bytes) widths = {GX_SHARDS_OFF, 0};
+        std::vector<uint32_t> widths = {0}; /* per-program choices ride on the chunks */
         for (uint32_t blk : blocks)
             for (uint32_t ept : epts) for (uint32_t w : widths) {
                 if (batch_plan_shape(b, blk, ept, w) != GX_OK) continue;
@@ -576,7 +596,7 @@ void gx_server::run() {
                                       std::max(max_ctx, sl.persist.max_ctx), cap_chunks);
             }
             std::vector<gx_chunk> table;
-            make_chunks(items, chunk_events, table, jit ? &prog_slot : nullptr);
+            make_chunks(items, chunk_events, table, jit ? &prog_slot : nullptr, jit ? jk.wc_max_bits : 0);
             if (rc == GX_OK) {
                 memcpy(sl.host_table, table.data(), table.size() * sizeof(gx_chunk));
                 /* the count travels in the same pinned buffer, in the entry after the table */

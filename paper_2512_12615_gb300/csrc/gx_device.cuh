@@ -420,6 +420,22 @@ __device__ __forceinline__ u64 hash_find_word(const gx_dmap &m, u64 kw, u64 *sta
     return 0;
 }
 
+/*
+ * The same lookup for a map whose keys are never deleted (GX_MAP_F_NO_DELETE).  A slot's
+ * key word is written once, before the slot is published as FULL, and a FULL slot never
+ * changes again; so a plain (L1-cached) read of {state, key} that shows FULL and the
+ * searched non-zero key is the final truth, and hot keys are served from L1 instead of
+ * one L2 slice.  Anything else (a stale or empty line, another key, key 0) takes the
+ * ordered probe above.
+ */
+template <int KS, int VS>
+__device__ __forceinline__ u64 hash_find_word_nd(const gx_dmap &m, u64 kw, u64 *stats) {
+    const u64 i = mix64(0x9E3779B97F4A7C15ull ^ (u64)KS ^ kw) & m.mask;
+    const ulonglong2 v = *(const ulonglong2 *)(m.slots + i * 16u);
+    if ((u32)v.x == GX_SLOT_FULL && v.y == kw && kw != 0) return (u64)(m.values + i * (u64)VS);
+    return hash_find_word<KS, VS>(m, kw, stats);
+}
+
 /* lookup with lanes that look up the same (<= 8 byte) key sharing one probe */
 __device__ __noinline__ u64 map_lookup(const gx_dmap &m, const uint8_t *k, u32 exec, u64 *stats) {
     if (m.type == GX_MAP_ARRAY) {
@@ -545,6 +561,7 @@ struct ExecEnv {
     u64 budget;
     u32 slot;      /* which program of a multi-program specialised kernel (chunk.pad); 0 in plain mode */
     u32 wc_bits;   /* block-private combining: log2 cache entries per map, 0 = off */
+    u32 wc_agg;    /* updates that miss the cache are warp-aggregated */
     uint8_t *shard; /* the block's combining area (shared memory) */
 };
 
@@ -633,104 +650,141 @@ __device__ __forceinline__ void wc_flush_word(void *g, u64 v) {
 }
 
 /*
- * The launch skeleton shared by the interpreter and by load-time specialised programs.
- * Plain mode (P.mode == 0): block b stages the program image into shared memory and
- * processes tiles b*ept .. b*ept+ept-1 of blockDim events.  Persistent mode (1): blocks
- * claim chunks {program image, event range} from an atomic cursor until the table is
- * exhausted, restaging the image only when the program changes.  Each warp transposes
- * its 32 records into shared memory, then `run_event` executes one event per lane and
- * returns R0.
+ * One chunk's events: warp w takes tiles begin + 32w, begin + 32w + blockDim, ...; each
+ * warp transposes its 32 records into shared memory, then `run_event` executes one event
+ * per lane and returns R0.
  */
-template <typename RunEvent, typename Init, typename Flush>
-__device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_event, Init wc_init, Flush wc_flush) {
+template <typename RunEvent>
+__device__ __forceinline__ void chunk_tiles(const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all, RunEvent run_event) {
+    const u32 warp = threadIdx.x >> 5, lane = lane_id();
+    const u32 cw = ch.ctx_size / 8;
+    u64 *ctxw = ctx_all + warp * cw * 32;
+    for (u64 first = ch.begin + (u64)warp * 32; first < ch.end; first += blockDim.x) {
+        load_ctx_tile(ctxw, ch.events, first, ch.end, cw);
+        const u64 idx = first + lane;
+        const bool valid = idx < ch.end;
+        u64 r0 = run_event(env, ctxw, valid, ch.idx_base + idx);
+        if (valid && ch.ret_out) ch.ret_out[idx] = (long long)r0;
+        __syncwarp();
+    }
+}
+
+/* ExecEnv of the program image staged at smem */
+__device__ __forceinline__ ExecEnv stage_env_at(uint8_t *smem, u32 shard_off, u32 slot, u32 wcp) {
+    const gx_dprog_hdr *hdr = (const gx_dprog_hdr *)smem;
+    ExecEnv env;
+    env.maps = (const gx_dmap *)(smem + sizeof(gx_dprog_hdr));
+    env.uops = (const u64 *)(smem + sizeof(gx_dprog_hdr) + hdr->n_maps * sizeof(gx_dmap));
+    env.stats = hdr->stats;
+    env.budget = hdr->budget;
+    env.slot = slot;
+    env.wc_bits = wcp & 0xFFu;
+    env.wc_agg = (wcp >> 8) & 1u;
+    env.shard = smem + shard_off;
+    return env;
+}
+
+__device__ __forceinline__ ExecEnv stage_env(uint8_t *smem, const ExecParams &P, u32 slot, u32 wcp) {
+    const gx_dprog_hdr *hdr = (const gx_dprog_hdr *)smem;
+    ExecEnv env;
+    env.maps = (const gx_dmap *)(smem + sizeof(gx_dprog_hdr));
+    env.uops = (const u64 *)(smem + sizeof(gx_dprog_hdr) + hdr->n_maps * sizeof(gx_dmap));
+    env.stats = hdr->stats;
+    env.budget = hdr->budget;
+    env.slot = slot;
+    env.wc_bits = wcp & 0xFFu;
+    env.wc_agg = (wcp >> 8) & 1u;
+    env.shard = smem + P.shard_off;
+    return env;
+}
+
+/*
+ * The launch skeleton shared by the interpreter and by load-time specialised programs.
+ * Plain mode (P.mode == 0): block b stages the program image into shared memory and runs
+ * events [b*ept*blockDim, (b+1)*ept*blockDim) as one chunk.  Persistent mode (1): blocks
+ * claim chunks {program image, event range} from an atomic cursor until the table is
+ * exhausted, restaging the image only when the program changes.  `run_chunk(env, chunk,
+ * ctx_area)` runs one chunk (chunk_tiles with the program's per-event code).  The
+ * combining area (wc_init / wc_flush) stays open across consecutive chunks of the same
+ * program and choice; its totals go to device memory when the program or choice changes
+ * and when the block runs out of work, while that program's image is still staged.
+ */
+template <typename RunChunk, typename Init, typename Flush>
+__device__ __forceinline__ void exec_tiles(const ExecParams &P, RunChunk run_chunk, Init wc_init, Flush wc_flush) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ u32 s_chunk;
     __shared__ const uint8_t *s_image;
-    const u32 warp = threadIdx.x >> 5, lane = lane_id();
-    const u32 warps = blockDim.x >> 5;
     u64 *ctx_all = (u64 *)(smem + P.image_area);
     if (P.mode == 0) {
         stage_image(smem, P.image, P.image_bytes);
-        const gx_dprog_hdr *hdr = (const gx_dprog_hdr *)smem;
-        ExecEnv env;
-        env.maps = (const gx_dmap *)(smem + sizeof(gx_dprog_hdr));
-        env.uops = (const u64 *)(smem + sizeof(gx_dprog_hdr) + hdr->n_maps * sizeof(gx_dmap));
-        env.stats = hdr->stats;
-        env.budget = hdr->budget;
-        env.slot = 0;
-        env.wc_bits = P.wc_bits;
-        env.shard = smem + P.shard_off;
-        if (P.wc_bits) {
+        const ExecEnv env = stage_env(smem, P, 0, P.wc_bits);
+        if (env.wc_bits) {
             wc_init(env);
             __syncthreads();
         }
-        const u32 cw = P.ctx_size / 8;
-        u64 *ctxw = ctx_all + warp * cw * 32;
-        const u64 tile0 = (u64)blockIdx.x * blockDim.x * P.ept;
-        for (u32 e = 0; e < P.ept; e++) {
-            const u64 first = tile0 + (u64)e * blockDim.x + warp * 32;
-            if (first >= P.n) break; /* warp-uniform */
-            load_ctx_tile(ctxw, P.events, first, P.n, cw);
-            const u64 idx = first + lane;
-            const bool valid = idx < P.n;
-            u64 r0 = run_event(env, ctxw, valid, P.idx_base + idx);
-            if (valid && P.ret_out) P.ret_out[idx] = (long long)r0;
-            __syncwarp();
-        }
-        if (P.wc_bits) {
+        gx_chunk ch;
+        ch.image = P.image;
+        ch.events = P.events;
+        ch.ret_out = P.ret_out;
+        ch.begin = (u64)blockIdx.x * blockDim.x * P.ept;
+        ch.end = ch.begin + (u64)blockDim.x * P.ept < P.n ? ch.begin + (u64)blockDim.x * P.ept : P.n;
+        ch.idx_base = P.idx_base;
+        ch.image_bytes = P.image_bytes;
+        ch.ctx_size = P.ctx_size;
+        ch.pad = 0;
+        run_chunk(env, ch, ctx_all);
+        if (env.wc_bits) {
             __syncthreads();
             wc_flush(env);
         }
         return;
     }
-    /* persistent mode: claim chunks until the table is exhausted */
     const u32 nchunks = P.nchunks_dev ? *P.nchunks_dev : P.nchunks;
     if (threadIdx.x == 0) s_image = nullptr;
+    ExecEnv open;
+    u32 open_wcp = 0;
+    bool is_open = false; /* block-uniform */
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_chunk = atomicAdd(P.cursor, 1u);
         __syncthreads();
         const u32 c = s_chunk;
-        if (c >= nchunks) break;
-        const gx_chunk ch = P.chunks[c];
+        const bool done = c >= nchunks;
+        gx_chunk ch;
+        u32 wcp = 0;
+        if (!done) {
+            ch = P.chunks[c];
+            wcp = (ch.pad >> 63) ? (u32)(ch.pad >> 32) & 0x1FFu : P.wc_bits; /* the chunk's own choice */
+        }
+        if (is_open && (done || (u32)ch.pad != open.slot || wcp != open_wcp)) {
+            wc_flush(open);
+            __syncthreads();
+            is_open = false;
+        }
+        if (done) break;
         if (ch.image != s_image) {
             stage_image(smem, ch.image, ch.image_bytes);
             if (threadIdx.x == 0) s_image = ch.image;
         }
-        const gx_dprog_hdr *hdr = (const gx_dprog_hdr *)smem;
-        ExecEnv env;
-        env.maps = (const gx_dmap *)(smem + sizeof(gx_dprog_hdr));
-        env.uops = (const u64 *)(smem + sizeof(gx_dprog_hdr) + hdr->n_maps * sizeof(gx_dmap));
-        env.stats = hdr->stats;
-        env.budget = hdr->budget;
-        env.slot = (u32)ch.pad;
-        env.wc_bits = P.wc_bits;
-        env.shard = smem + P.shard_off;
-        if (P.wc_bits) {
+        const ExecEnv env = stage_env(smem, P, (u32)ch.pad, wcp);
+        if (env.wc_bits && !is_open) {
             wc_init(env);
             __syncthreads();
+            open = env;
+            open_wcp = wcp;
+            is_open = true;
         }
-        const u32 cw = ch.ctx_size / 8;
-        u64 *ctxw = ctx_all + warp * cw * 32;
-        for (u64 first = ch.begin + (u64)warp * 32; first < ch.end; first += (u64)warps * 32) {
-            load_ctx_tile(ctxw, ch.events, first, ch.end, cw);
-            const u64 idx = first + lane;
-            const bool valid = idx < ch.end;
-            u64 r0 = run_event(env, ctxw, valid, ch.idx_base + idx);
-            if (valid && ch.ret_out) ch.ret_out[idx] = (long long)r0;
-            __syncwarp();
-        }
-        if (P.wc_bits) {
-            __syncthreads();
-            wc_flush(env);
-        }
+        run_chunk(env, ch, ctx_all);
     }
 }
 
-/* the interpreter: no block-private combining */
+/* the interpreter: per-event code inline, no block-private combining */
 template <typename RunEvent>
 __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_event) {
-    exec_tiles(P, run_event, [](const ExecEnv &) {}, [](const ExecEnv &) {});
+    exec_tiles(
+        P,
+        [&](const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all) { chunk_tiles(env, ch, ctx_all, run_event); },
+        [](const ExecEnv &) {}, [](const ExecEnv &) {});
 }
 
 } // namespace gx

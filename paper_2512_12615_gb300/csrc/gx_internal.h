@@ -22,6 +22,7 @@ struct InsnInfo {
     int8_t map = -1;        /* helper call: map index in R1 on every path, -2 if it varies */
     int16_t a2 = ARG_UNSET; /* helper call: constant stack offset of R2 on every path (else ARG_VARIES) */
     int16_t a3 = ARG_UNSET; /* same for R3 */
+    uint8_t stk_any = 0;    /* some path reaches the stack through this load / store / atomic */
     int8_t vmap = -1;       /* update of map memory (atomic, atomic max/min helper): the map on every path,
                                -2 if it varies or is not always a map value */
     int16_t voff = ARG_UNSET; /* ... and the constant byte offset within the value (else ARG_VARIES) */

@@ -141,8 +141,9 @@ typedef struct gx_exec_params {
     const gx_chunk *chunks; /* persistent mode */
     unsigned int *cursor;   /* persistent mode: next chunk to claim */
     const unsigned int *nchunks_dev; /* persistent mode: if set, the chunk count is read here */
-    uint32_t wc_bits;      /* specialised programs: log2 entries of each map's combining cache; 0 = no
-                              block-private combining (updates go to device memory) */
+    uint32_t wc_bits;      /* specialised programs: bits 0-7 log2 entries of each map's combining cache,
+                              0 = no block-private combining (updates go to device memory); bit 8:
+                              updates that miss the cache are warp-aggregated */
     uint32_t shard_off;    /* byte offset of the combining area in dynamic shared memory */
 } gx_exec_params;
 

@@ -54,6 +54,8 @@ struct gx_prog {
     unsigned long long *dstats = nullptr;
     uint64_t launches = 0;
     std::map<int, gx_launch> tuned; /* log2(n) bucket -> shape */
+    uint32_t pref_shards = 0;       /* tuned gx_launch.shards of this program in batches and ticks */
+    bool pref_tuned = false;
     /* load-time specialisation (GX_PROG_JIT) */
     gx::JitProgram jp;
     gx::JitKernel jk;
@@ -72,6 +74,10 @@ int dalloc(gx_ctx *c, uint64_t bytes, void **out);
 void dfree(gx_ctx *c, void *p, uint64_t bytes);
 int cuda_status(cudaError_t e);
 uint64_t exec_smem(uint32_t image_area, uint32_t block, uint32_t ctx_size);
+bool shards_valid(uint32_t shards);
+uint32_t shards_param(uint32_t shards, uint32_t default_bits);
+/* choose p->pref_shards by timing OFF / default / aggregated misses on a sample (scratch maps) */
+int tune_shards(gx_prog *p, const void *events, uint64_t n, cudaStream_t s);
 int ensure_smem(gx_ctx *c, uint64_t smem);
 int tuned_launch(gx_prog *p, uint64_t n, gx_launch *out);
 } // namespace gx

@@ -280,10 +280,44 @@ std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, 
           << "uint8_t *e_ = wc_entry(env.shard + " << sm->tags_off << ", env.shard + " << sm->acc_off << ", b_, "
           << sm->stride << "u, a_ - " << ii.voff << "ull); "
           << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); "
+          << "else if (env.wc_agg) agg_update" << t << "(a_, " << val << ", __activemask()); "
           << "else plain_atomic" << t << "((void *)a_, " << val << "); ";
     }
     o << "} else " << global;
     return o.str();
+}
+
+/*
+ * The eBPF stack as 64 scalar slot variables s0..s63 (bytes 8k..8k+7 of the 512-byte
+ * frame, little-endian), so the compiler keeps the live ones in registers.  Used when the
+ * verifier proved every stack access has one constant offset.  Helpers that read stack
+ * memory get the bytes copied into `stk_mem` (which R10 points into) just before the call.
+ */
+std::string stk_load(int abs, int size, bool sign) {
+    const std::string v = "s" + std::to_string(abs / 8);
+    const int b = abs % 8;
+    if (size == 8) return v;
+    const char *t = size == 4 ? (sign ? "int32_t" : "uint32_t") : size == 2 ? (sign ? "int16_t" : "uint16_t")
+                                                                            : (sign ? "int8_t" : "uint8_t");
+    std::string x = "(" + std::string(t) + ")(" + v + (b ? " >> " + std::to_string(8 * b) : "") + ")";
+    return sign ? "(u64)(s64)" + x : "(u64)" + x;
+}
+
+std::string stk_store(int abs, int size, const std::string &val) {
+    const std::string v = "s" + std::to_string(abs / 8);
+    const int b = abs % 8;
+    if (size == 8) return v + " = (u64)(" + val + ");";
+    const std::string m = hex64(size == 4 ? 0xFFFFFFFFull : size == 2 ? 0xFFFFull : 0xFFull);
+    const std::string sh = std::to_string(8 * b);
+    return v + " = (" + v + " & ~(" + m + " << " + sh + ")) | (((u64)(" + val + ") & " + m + ") << " + sh + ");";
+}
+
+/* copy slots covering stack bytes [lo, 512) into stk_mem (lo = frame offset + 512) */
+std::string stk_materialise(int lo) {
+    std::string o;
+    for (int k = std::max(0, lo) / 8; k < GX_STACK_BYTES / 8; k++)
+        o += "stk_mem[" + std::to_string(k) + "] = s" + std::to_string(k) + "; ";
+    return o;
 }
 
 /* one program -> `__device__ u64 gx_body_<slot>(env, ctxw, valid, ev_idx)` */
@@ -305,16 +339,37 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             target[t] = 1;
         }
     }
+    /* scalar stack unless some load / store / atomic reaches the stack at a varying offset */
+    bool scalar = true;
+    for (uint32_t pc = 0; pc < n; pc++)
+        if (p.info[pc].visited && p.info[pc].stk_any && p.info[pc].kind != MK_STACK) scalar = false;
     std::ostringstream o;
     o << "__device__ __forceinline__ u64 gx_body_" << slot
       << "(const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {\n"
       << "  if (!valid) return 0;\n"
-      << "  const u32 lane = threadIdx.x & 31;\n"
-      << "  u64 stack[" << GX_STACK_BYTES / 8 << "];\n"
-      << "  u64 r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0;\n"
-      << "  u64 r10 = (u64)(stack + " << GX_STACK_BYTES / 8 << ");\n"
+      << "  const u32 lane = threadIdx.x & 31;\n";
+    if (scalar) {
+        o << "  u64 stk_mem[" << GX_STACK_BYTES / 8 << "];\n  u64 ";
+        for (int k = 0; k < GX_STACK_BYTES / 8; k++) o << (k ? ", s" : "s") << k << " = 0";
+        o << ";\n  u64 r10 = (u64)(stk_mem + " << GX_STACK_BYTES / 8 << ");\n";
+    } else {
+        o << "  u64 stack[" << GX_STACK_BYTES / 8 << "];\n"
+          << "  u64 r10 = (u64)(stack + " << GX_STACK_BYTES / 8 << ");\n";
+    }
+    o << "  u64 r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0;\n"
       << "  u64 back = 0;\n"
       << "  (void)lane; (void)ev_idx; (void)back; (void)r10;\n";
+    /* before a helper that reads stack memory through R2 / R3 */
+    auto mat = [&](const InsnInfo &ii, bool r3_mem) -> std::string {
+        if (!scalar) return "";
+        int lo = GX_STACK_BYTES;
+        for (int16_t a : {ii.a2, r3_mem ? ii.a3 : InsnInfo::ARG_UNSET}) {
+            if (a == InsnInfo::ARG_UNSET) continue;
+            if (a == InsnInfo::ARG_VARIES || a >= 0 || a < -GX_STACK_BYTES) lo = 0;
+            else lo = std::min(lo, a + GX_STACK_BYTES);
+        }
+        return lo < GX_STACK_BYTES ? stk_materialise(lo) : "";
+    };
     const uint64_t budget = p.budget;
     auto jump = [&](uint32_t pc, int64_t tgt) -> std::string {
         std::string g = "goto L" + std::to_string(tgt) + ";";
@@ -387,21 +442,34 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             }
             if (code == 0x80) {
                 std::string m = ii.map >= 0 ? "env.maps[" + std::to_string(ii.map) + "]" : "env.maps[r1]";
+                const bool inline_lookup = imm == GX_HELPER_MAP_LOOKUP && ii.map >= 0 && ii.map < (int)p.maps.size() &&
+                                           ii.a2 < 0 && ii.a2 >= -GX_STACK_BYTES &&
+                                           (p.maps[ii.map].type == GX_MAP_ARRAY ||
+                                            (p.maps[ii.map].type == GX_MAP_HASH &&
+                                             (p.maps[ii.map].key_size == 1 || p.maps[ii.map].key_size == 2 ||
+                                              p.maps[ii.map].key_size == 4 || p.maps[ii.map].key_size == 8)));
+                if (!inline_lookup && imm != GX_HELPER_ATOMIC_MAX_U64 && imm != GX_HELPER_ATOMIC_MIN_U64 &&
+                    imm != GX_HELPER_RINGBUF_SUBMIT && imm != GX_HELPER_RINGBUF_DISCARD &&
+                    imm != GX_HELPER_RINGBUF_RESERVE)
+                    o << mat(ii, imm == GX_HELPER_MAP_UPDATE);
                 switch (imm) {
                 case GX_HELPER_MAP_LOOKUP: {
                     /* one map and a key at a known stack slot: inline, per lane, layout as constants */
                     const gx_map_spec *ms = ii.map >= 0 && ii.map < (int)p.maps.size() ? &p.maps[ii.map] : nullptr;
-                    const bool key_known = ii.a2 < 0 && ii.a2 >= -GX_STACK_BYTES;
                     const uint32_t vs = ms ? (ms->value_size + 7u) & ~7u : 0;
-                    const std::string key = "(const uint8_t *)stack + " + std::to_string(ii.a2 + GX_STACK_BYTES);
-                    if (ms && key_known && ms->type == GX_MAP_ARRAY) {
-                        o << "{ const u32 k_ = (u32)load_sz<4, false>(" << key << "); r0 = k_ < " << ms->max_entries
+                    auto key = [&](int ks) {
+                        const int abs = ii.a2 + GX_STACK_BYTES;
+                        if (scalar) return stk_load(abs, ks, false);
+                        return "load_sz<" + std::to_string(ks) + ", false>((const uint8_t *)stack + " +
+                               std::to_string(abs) + ")";
+                    };
+                    if (inline_lookup && ms->type == GX_MAP_ARRAY) {
+                        o << "{ const u32 k_ = (u32)" << key(4) << "; r0 = k_ < " << ms->max_entries
                           << "u ? (u64)(" << m << ".values + (u64)k_ * " << vs << "u) : 0ull; }";
-                    } else if (ms && key_known && ms->type == GX_MAP_HASH &&
-                               (ms->key_size == 1 || ms->key_size == 2 || ms->key_size == 4 || ms->key_size == 8)) {
+                    } else if (inline_lookup) {
                         const std::string ks = std::to_string(ms->key_size);
-                        o << "r0 = hash_find_word<" << ks << ", " << vs << ">(" << m << ", load_sz<" << ks << ", false>("
-                          << key << "), env.stats);";
+                        o << "r0 = hash_find_word" << ((ms->flags & GX_MAP_F_NO_DELETE) ? "_nd<" : "<") << ks << ", "
+                          << vs << ">(" << m << ", " << key(ms->key_size) << ", env.stats);";
                     } else {
                         o << "r0 = map_lookup(" << m << ", (const uint8_t *)r2, __activemask(), env.stats);";
                     }
@@ -462,6 +530,8 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             if (ii.kind == MK_CTX)
                 o << R(dst) << " = " << ld << "(const uint8_t *)(ctxw + " << ((ii.off >> 3) << 5) << " + lane) + "
                   << (ii.off & 7) << ");";
+            else if (ii.kind == MK_STACK && scalar)
+                o << R(dst) << " = " << stk_load(ii.off + GX_STACK_BYTES, size, sign) << ";";
             else if (ii.kind == MK_STACK)
                 o << R(dst) << " = " << ld << "(const uint8_t *)stack + " << ii.off + GX_STACK_BYTES << ");";
             else
@@ -471,6 +541,28 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         }
         case 2: case 3: {
             int size = size_of(op);
+            if (ii.kind == MK_STACK && scalar) {
+                const int abs = ii.off + GX_STACK_BYTES;
+                if ((op & 0xE0) != 0xC0) {
+                    o << stk_store(abs, size, cls == 3 ? R(src) : hex64((uint64_t)(int64_t)imm));
+                    break;
+                }
+                const std::string old_v = stk_load(abs, size, false), sr = R(src);
+                const std::string mask = size == 4 ? " & 0xFFFFFFFFull" : "";
+                o << "{ const u64 o_ = " << old_v << "; ";
+                if (imm == 0xE1) {
+                    o << stk_store(abs, size, sr) << " " << sr << " = o_; }";
+                } else if (imm == 0xF1) {
+                    o << "if (o_ == (r0" << mask << ")) " << stk_store(abs, size, sr) << " r0 = o_; }";
+                } else {
+                    int b = imm & ~1;
+                    const char *opx = b == 0x00 ? "+" : b == 0x40 ? "|" : b == 0x50 ? "&" : "^";
+                    o << stk_store(abs, size, "o_ " + std::string(opx) + " " + sr) << " ";
+                    if (imm & 1) o << sr << " = o_; ";
+                    o << "}";
+                }
+                break;
+            }
             std::string addr = ii.kind == MK_STACK
                                    ? "(u64)((uint8_t *)stack + " + std::to_string(ii.off + GX_STACK_BYTES) + ")"
                                    : "(" + R(dst) + " + " + hex64((uint64_t)(int64_t)off) + ")";
@@ -566,16 +658,34 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
         }
         return h + "  }";
     };
-    src += "} // namespace gx\n\nextern \"C\" __global__ void __launch_bounds__(256) gx_jit_kernel(gx::ExecParams P) {\n"
-           "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx::u64 *ctxw, bool valid, gx::u64 ev_idx) -> gx::u64 {\n";
-    if (progs.size() == 1) {
-        src += "    return gx::gx_body_0(env, ctxw, valid, ev_idx);\n";
-    } else {
-        src += "    switch (env.slot) {\n";
+    /*
+     * Several programs: each one's chunk loop is its own out-of-line function, so every
+     * program gets its own register allocation (one kernel-wide allocation over all bodies
+     * spills) and the dispatch costs one call per chunk, not per event.
+     */
+    auto chunk_loop = [](size_t i) {
+        return "chunk_tiles(env, ch, ctx_all, [](const ExecEnv &e, const u64 *c, bool v, u64 x) -> u64 { return gx_body_" +
+               std::to_string(i) + "(e, c, v, x); });";
+    };
+    if (progs.size() > 1)
         for (size_t i = 0; i < progs.size(); i++)
-            src += "    case " + std::to_string(i) + ": return gx::gx_body_" + std::to_string(i) +
-                   "(env, ctxw, valid, ev_idx);\n";
-        src += "    }\n    return 0;\n";
+            src += "__device__ __noinline__ void gx_chunk_" + std::to_string(i) +
+                   "(const gx_chunk ch, u32 wcp, u32 shard_off, u64 *ctx_all) {\n"
+                   "  extern __shared__ __align__(16) uint8_t smem[];\n"
+                   "  const ExecEnv env = stage_env_at(smem, shard_off, (u32)ch.pad, wcp);\n  " +
+                   chunk_loop(i) + "\n}\n";
+    /* several programs: at most 48 registers, so five 256-thread blocks fit on an SM whatever the mix */
+    src += std::string("} // namespace gx\n\nextern \"C\" __global__ void __launch_bounds__(") +
+           (progs.size() > 1 ? "256, 5" : "256") + ") gx_jit_kernel(gx::ExecParams P) {\n"
+           "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx_chunk &ch, gx::u64 *ctx_all) {\n";
+    if (progs.size() == 1) {
+        src += "    using namespace gx;\n    " + chunk_loop(0) + "\n";
+    } else {
+        src += "    extern __shared__ __align__(16) uint8_t smem_base[];\n    switch (env.slot) {\n";
+        for (size_t i = 0; i < progs.size(); i++)
+            src += "    case " + std::to_string(i) + ": gx::gx_chunk_" + std::to_string(i) +
+                   "(ch, env.wc_bits | (env.wc_agg << 8), (gx::u32)(env.shard - smem_base), ctx_all); break;\n";
+        src += "    }\n";
     }
     src += "  },\n" + hook("init") + ",\n" + hook("flush") + ");\n}\n";
     return src;

@@ -674,6 +674,7 @@ struct Verifier {
     /* ---------------------------------------------------- memory checks */
     int note(u32 pc, uint8_t kind, int off) {
         InsnInfo &ii = out->info[pc];
+        if (kind == MK_STACK) ii.stk_any = 1;
         if (ii.kind == MK_NONE) {
             ii.kind = kind;
             ii.off = (int16_t)off;
@@ -1363,6 +1364,7 @@ struct Verifier {
         case GX_HELPER_MAP_DELETE: {
             if (need_map(1)) return GX_E_VERIFY;
             if (det) return fail(pc, "map delete in deterministic mode");
+            if (maps[s.r[1].map].flags & GX_MAP_F_NO_DELETE) return fail(pc, "map delete on a map created without deletes");
             bool t;
             if (mem_arg(pc, s, s.r[2], maps[s.r[1].map].key_size, "delete key", &t, nullptr)) return GX_E_VERIFY;
             r0 = sc_unknown();
@@ -1513,6 +1515,7 @@ int verify_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, u
             ok = m.key_size >= 1 && m.key_size <= GX_MAX_KEY && m.value_size >= 1 && m.value_size <= GX_MAX_VALUE &&
                  m.max_entries >= 1 && m.max_entries <= (1u << 30);
         if (m.type == GX_MAP_RINGBUF) ok = m.max_entries >= 4096 && (m.max_entries & (m.max_entries - 1)) == 0;
+        if ((m.flags & ~GX_MAP_F_NO_DELETE) || (m.flags && m.type != GX_MAP_HASH) || m.reserved) ok = false;
         if (!ok) {
             out.log = "invalid map spec at index " + std::to_string(i);
             return GX_EINVAL;

@@ -28,7 +28,16 @@ u32, u64, i32, i64, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes
 
 
 class MapSpec(ctypes.Structure):
-    _fields_ = [("type", u32), ("key_size", u32), ("value_size", u32), ("max_entries", u32)]
+    _fields_ = [("type", u32), ("key_size", u32), ("value_size", u32), ("max_entries", u32), ("flags", u32),
+                ("reserved", u32)]
+
+
+MAP_F_NO_DELETE = 1
+
+
+def _specs(map_specs: Sequence[dict]):
+    return (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"],
+                                                        s.get("flags", 0), 0) for s in map_specs])
 
 
 class ProgOpts(ctypes.Structure):
@@ -44,6 +53,7 @@ class Analysis(ctypes.Structure):
 
 
 SHARDS_OFF = 255
+SHARDS_AGG = 0x100  # OR into a width: warp-aggregate the updates that miss the combining cache
 
 
 def _launch(launch) -> Optional[Launch]:
@@ -181,8 +191,7 @@ def verify(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, determin
            insn_budget: int = 0) -> Tuple[int, str]:
     """Host-only verification: (status, log)."""
     insns = np.ascontiguousarray(insns, dtype=np.uint64)
-    specs = (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"])
-                                                   for s in map_specs])
+    specs = _specs(map_specs)
     opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
     log = ctypes.create_string_buffer(1024)
     rc = lib().gx_verify(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), log, 1024)
@@ -193,8 +202,7 @@ def analyze(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, determi
             insn_budget: int = 0) -> Tuple[int, Analysis, str]:
     """Host-only verification plus what it proved: (status, gx_analysis, log)."""
     insns = np.ascontiguousarray(insns, dtype=np.uint64)
-    specs = (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"])
-                                                   for s in map_specs])
+    specs = _specs(map_specs)
     opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
     out = Analysis()
     log = ctypes.create_string_buffer(1024)
@@ -210,8 +218,7 @@ def jit_check(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, deter
               insn_budget: int = 0) -> Tuple[int, str]:
     """Host-only: verify and compile the specialised form (no device): (status, log)."""
     insns = np.ascontiguousarray(insns, dtype=np.uint64)
-    specs = (MapSpec * max(1, len(map_specs)))(*[MapSpec(s["type"], s["key_size"], s["value_size"], s["max_entries"])
-                                                   for s in map_specs])
+    specs = _specs(map_specs)
     opts = ProgOpts(ctx_size, int(deterministic), insn_budget, PROG_JIT, 0)
     log = ctypes.create_string_buffer(8192)
     rc = lib().gx_jit_check(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), log, 8192)
@@ -234,15 +241,18 @@ class Context:
 
 
 class Map:
-    def __init__(self, ctx: Context, type: int, key_size: int, value_size: int, max_entries: int) -> None:
+    def __init__(self, ctx: Context, type: int, key_size: int, value_size: int, max_entries: int,
+                 flags: int = 0) -> None:
         h = ctypes.c_void_p()
-        check(lib().gx_map_create(ctx.h, type, key_size, value_size, max_entries, 0, ctypes.byref(h)), "gx_map_create")
-        self.h, self.ctx = h, ctx
+        check(lib().gx_map_create(ctx.h, type, key_size, value_size, max_entries, flags, ctypes.byref(h)),
+              "gx_map_create")
+        self.h, self.ctx, self.flags = h, ctx, flags
         self.type, self.key_size, self.value_size, self.max_entries = type, key_size, value_size, max_entries
 
     @classmethod
     def from_spec(cls, ctx: Context, spec: dict) -> "Map":
-        return cls(ctx, spec["type"], spec["key_size"], spec["value_size"], spec["max_entries"])
+        return cls(ctx, spec["type"], spec["key_size"], spec["value_size"], spec["max_entries"],
+                   flags=spec.get("flags", 0))
 
     def destroy(self) -> None:
         if self.h:

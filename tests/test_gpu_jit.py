@@ -90,3 +90,45 @@ def test_budget_trip_jit(ctx):
     p.run(device_events(ev), 77, ret_out=ret)
     st = p.status(reset=True)
     assert st.status == gx.E_BUDGET and st.budget_trips == 77 and int(ret.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("insert_only", [False, True])
+def test_page_heat_hash_flavours_two_launches(ctx, insert_only):
+    """Ordered probes (ordinary hash map) and L1-first probes (insert-only map): the second
+    launch finds every key published, the first one races inserts against lookups."""
+    import paper_2512_12615_gb300 as gx
+    import oracle as O
+    from tests.parity import assert_same, gpu_maps, snapshot_gpu, snapshot_oracle
+
+    prog, specs, cs = P.page_heat()
+    specs = [dict(s) for s in specs]
+    if insert_only:
+        assert specs[0]["flags"] == gx.MAP_F_NO_DELETE
+    else:
+        specs[0].pop("flags", None)
+    ev = gen.pageheat_events(150_001, seed=77)
+    gm = gpu_maps(ctx, specs)
+    p = gx.Program(ctx, prog, gm, cs, deterministic=True, jit=True)
+    dev = device_events(ev)
+    om = O.maps_from_specs(specs)
+    for _ in range(2):
+        p.run(dev, len(ev))
+        O.run(prog, om, ev, cs)
+    torch.cuda.synchronize()
+    assert p.status().status == 0
+    assert_same(snapshot_gpu(gm), snapshot_oracle(om))
+
+
+def test_map_flags_are_checked(ctx):
+    import paper_2512_12615_gb300 as gx
+
+    with pytest.raises(gx.GxError):
+        gx.Map(ctx, gx.MAP_ARRAY, 4, 8, 16, flags=gx.MAP_F_NO_DELETE)
+    with pytest.raises(gx.GxError):
+        gx.Map(ctx, gx.MAP_HASH, 8, 8, 16, flags=2)
+    m = gx.Map(ctx, gx.MAP_HASH, 8, 8, 16, flags=gx.MAP_F_NO_DELETE)
+    prog = assemble(["mov r6 r1", "ldx8 r7 r6 0", "stx8 r10 -8 r7", "ld_map r1 0", "mov r2 r10", "add r2 -8",
+                     "call map_delete_elem", "mov r0 0", "exit"]).prog()
+    with pytest.raises(gx.GxError):
+        gx.Program(ctx, prog, [m], 16)
+    m.destroy()

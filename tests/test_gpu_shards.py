@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 OFF = 255
+AGG = 0x100
 
 # array map 0: 8 values of 64 bytes, one update kind per word; hash map 1: 64 keys, same layout
 ALLOPS = """
@@ -143,7 +144,7 @@ def test_allops_is_combinable():
     assert info.combinable_maps == 3
 
 
-@pytest.mark.parametrize("shards", [OFF, 2, 3, 0, 10])
+@pytest.mark.parametrize("shards", [OFF, 2, 3, 0, 10, 2 | AGG, AGG])
 @pytest.mark.parametrize("shape", [(64, 3), (256, 8)])
 def test_allops_every_width(ctx, shards, shape):
     ev = allops_events(50_003, seed=7 + shards)
@@ -156,7 +157,7 @@ def test_allops_tiny_batch(ctx):
                  init=allops_init())
 
 
-@pytest.mark.parametrize("shards", [OFF, 2, 0])
+@pytest.mark.parametrize("shards", [OFF, 2, 0, 2 | AGG])
 def test_page_heat_widths(ctx, shards):
     prog, specs, cs = P.page_heat()
     ev = gen.pageheat_events(300_007, seed=41)
@@ -175,12 +176,13 @@ def test_counting_and_latency_widths(ctx, shards):
 
 
 @pytest.mark.parametrize("p", [1, 8, 22, 40, 57])
-def test_random_programs_narrow_cache(ctx, p):
+@pytest.mark.parametrize("agg", [0, AGG])
+def test_random_programs_narrow_cache(ctx, p, agg):
     prog, specs, cs = P.batch_programs()[p]
-    run_both(ctx, prog, specs, cs, gen.uniform_events(30_011, seed=500 + p), jit=True, launch=(256, 4, 2))
+    run_both(ctx, prog, specs, cs, gen.uniform_events(30_011, seed=500 + p), jit=True, launch=(256, 4, 2 | agg))
 
 
-@pytest.mark.parametrize("shards", [OFF, 3, 0])
+@pytest.mark.parametrize("shards", [OFF, 3, 0, 3 | AGG])
 def test_batch_kernel_with_shards(ctx, shards):
     """The persistent multi-program kernel flushes each chunk's combined updates."""
     import paper_2512_12615_gb300 as gx
@@ -219,6 +221,6 @@ def test_autotune_reports_a_width(ctx):
     gm = gpu_maps(ctx, specs)
     p = gx.Program(ctx, prog, gm, cs, deterministic=True, jit=True)
     block, ept, shards = p.autotune(device_events(ev), len(ev))
-    assert block in (128, 256) and 1 <= ept <= 64 and shards in (0, 6, OFF)
+    assert block in (128, 256) and 1 <= ept <= 64 and shards in (0, AGG, OFF)
     # tuning ran on scratch copies: the real maps are untouched
     assert len(gm[0].hash_items()) == 0 and not gm[1].array_values().any()

@@ -275,3 +275,22 @@ def test_det_rejects_mixed_atomic_operations_on_the_same_bytes():
     same_word = VALUE + ["mov r3 1", "atomic8 add r0 0 r3", "mov r1 r0", "mov r2 5", "call atomic_max_u64",
                          "out:", "mov r0 0", "exit"]
     rejected(same_word, [ARRAY], det=True, why="two different atomic operations")
+
+
+# ---------------------------------------------------------------- insert-only hash maps
+DEL = ["mov r6 r1", "ldx8 r7 r6 0", "stx8 r10 -8 r7", "ld_map r1 0", "mov r2 r10", "add r2 -8",
+       "call map_delete_elem", "mov r0 0", "exit"]
+
+
+def test_delete_allowed_on_an_ordinary_hash_map():
+    ok(DEL, [HASH])
+
+
+def test_rejects_delete_on_an_insert_only_hash_map():
+    rejected(DEL, [dict(HASH, flags=gx.MAP_F_NO_DELETE)], why="created without deletes")
+
+
+@pytest.mark.parametrize("spec", [dict(ARRAY, flags=gx.MAP_F_NO_DELETE), dict(HASH, flags=2), dict(RING, flags=1)])
+def test_rejects_bad_map_flags(spec):
+    rc, log = gx.verify(assemble(["mov r0 0", "exit"]).prog(), [spec], 32)
+    assert rc == gx.EINVAL and "invalid map spec" in log

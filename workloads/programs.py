@@ -32,8 +32,14 @@ def array_spec(n: int, value_size: int = 8) -> MapSpec:
     return dict(type=MAP_ARRAY, key_size=4, value_size=value_size, max_entries=n)
 
 
-def hash_spec(n: int, key_size: int = 8, value_size: int = 16) -> MapSpec:
-    return dict(type=MAP_HASH, key_size=key_size, value_size=value_size, max_entries=n)
+MAP_F_NO_DELETE = 1  # keys are never removed (the engine's insert-only hash maps)
+
+
+def hash_spec(n: int, key_size: int = 8, value_size: int = 16, insert_only: bool = False) -> MapSpec:
+    s = dict(type=MAP_HASH, key_size=key_size, value_size=value_size, max_entries=n)
+    if insert_only:
+        s["flags"] = MAP_F_NO_DELETE
+    return s
 
 
 def ringbuf_spec(nbytes: int) -> MapSpec:
@@ -174,7 +180,7 @@ def page_heat(max_entries: int = 1 << 20) -> Tuple[np.ndarray, List[MapSpec], in
     a.label("bad_out")
     a.mov("r0", 0)
     a.exit()
-    return a.prog(), [hash_spec(max_entries, 8, 16), array_spec(PAGE_HEAT_TALLY, 16)], 32
+    return a.prog(), [hash_spec(max_entries, 8, 16, insert_only=True), array_spec(PAGE_HEAT_TALLY, 16)], 32
 
 
 # --------------------------------------------------------------------------------------
@@ -443,7 +449,7 @@ def random_program(seed: int, target_len: int, use_hash: bool = True) -> Tuple[n
             init -= {"r1", "r2", "r3", "r4", "r5"}
     a.mov("r0", rng.choice(sorted(init - {"r0"}) or ["r7"]))
     a.exit()
-    maps = [array_spec(RANDOM_ARRAY_ENTRIES), hash_spec(RANDOM_HASH_ENTRIES, 8, 16)]
+    maps = [array_spec(RANDOM_ARRAY_ENTRIES), hash_spec(RANDOM_HASH_ENTRIES, 8, 16, insert_only=True)]
     return a.prog(), maps, 32
 
 
