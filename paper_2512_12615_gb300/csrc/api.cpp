@@ -99,7 +99,8 @@ uint32_t shards_param(uint32_t sh, uint32_t default_bits) {
 
 /* dynamic shared memory of one block: staged image(s) + transposed ctx tiles */
 uint64_t exec_smem(uint32_t image_area, uint32_t block, uint32_t ctx_size) {
-    return (uint64_t)image_area + (block / 32) * (uint64_t)(ctx_size / 8) * 256;
+    const uint32_t cw = ctx_size / 8;
+    return (uint64_t)image_area + (block / 32) * (uint64_t)cw * GX_CTX_ROW(cw) * 8;
 }
 
 int ensure_smem(gx_ctx *c, uint64_t smem) {
@@ -499,6 +500,7 @@ int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *
             p->jp.info = v.info;
             p->jp.maps = specs;
             p->jp.use = v.map_use;
+            p->jp.ctx_size = opts->ctx_size;
             p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
             if (opts->flags & GX_PROG_JIT) {
                 rc = jit_build({&p->jp}, p->jk, msg);

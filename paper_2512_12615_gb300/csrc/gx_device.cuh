@@ -533,8 +533,9 @@ __device__ __forceinline__ void stage_image(uint8_t *dst, const uint8_t *src, u3
     __syncthreads();
 }
 
-/* the warp's next 32 records -> transposed shared tile ctxw[word * 32 + record] */
+/* the warp's next 32 records -> transposed shared tile ctxw[word * GX_CTX_ROW(cw) + record] */
 __device__ __forceinline__ void load_ctx_tile(u64 *ctxw, const uint8_t *events, u64 first, u64 n, u32 cw) {
+    const u32 row = GX_CTX_ROW(cw);
     const u32 lane = lane_id();
     const u64 nrec = n > first ? (n - first < 32 ? n - first : 32) : 0;
     const u32 chunks = cw * 16; /* 16-byte chunks in a full tile */
@@ -544,8 +545,8 @@ __device__ __forceinline__ void load_ctx_tile(u64 *ctxw, const uint8_t *events, 
         if (rec < nrec) {
             ulonglong2 v = __ldcs(src + c);
             u32 f = word % cw;
-            ctxw[f * 32 + rec] = v.x;
-            ctxw[(f + 1) * 32 + rec] = v.y;
+            ctxw[f * row + rec] = v.x;
+            ctxw[(f + 1) * row + rec] = v.y;
         }
     }
     __syncwarp();
@@ -562,6 +563,7 @@ struct ExecEnv {
     u32 slot;      /* which program of a multi-program specialised kernel (chunk.pad); 0 in plain mode */
     u32 wc_bits;   /* block-private combining: log2 cache entries per map, 0 = off */
     u32 wc_agg;    /* updates that miss the cache are warp-aggregated */
+    u32 ctx_row;   /* words between rows of the event tile (GX_CTX_ROW) */
     uint8_t *shard; /* the block's combining area (shared memory) */
 };
 
@@ -658,7 +660,7 @@ template <typename RunEvent>
 __device__ __forceinline__ void chunk_tiles(const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all, RunEvent run_event) {
     const u32 warp = threadIdx.x >> 5, lane = lane_id();
     const u32 cw = ch.ctx_size / 8;
-    u64 *ctxw = ctx_all + warp * cw * 32;
+    u64 *ctxw = ctx_all + warp * cw * GX_CTX_ROW(cw);
     for (u64 first = ch.begin + (u64)warp * 32; first < ch.end; first += blockDim.x) {
         load_ctx_tile(ctxw, ch.events, first, ch.end, cw);
         const u64 idx = first + lane;
@@ -680,6 +682,7 @@ __device__ __forceinline__ ExecEnv stage_env_at(uint8_t *smem, u32 shard_off, u3
     env.slot = slot;
     env.wc_bits = wcp & 0xFFu;
     env.wc_agg = (wcp >> 8) & 1u;
+    env.ctx_row = GX_CTX_ROW(hdr->ctx_size / 8);
     env.shard = smem + shard_off;
     return env;
 }
@@ -694,6 +697,7 @@ __device__ __forceinline__ ExecEnv stage_env(uint8_t *smem, const ExecParams &P,
     env.slot = slot;
     env.wc_bits = wcp & 0xFFu;
     env.wc_agg = (wcp >> 8) & 1u;
+    env.ctx_row = GX_CTX_ROW(hdr->ctx_size / 8);
     env.shard = smem + P.shard_off;
     return env;
 }

@@ -18,6 +18,7 @@ struct JitProgram {
     std::vector<InsnInfo> info;
     std::vector<gx_map_spec> maps; /* layouts become compile-time constants */
     std::vector<MapUse> use;       /* per map: may its updates be combined per block? */
+    uint32_t ctx_size = 8;         /* bytes per event record */
     uint64_t budget = 1ull << 16;
 };
 

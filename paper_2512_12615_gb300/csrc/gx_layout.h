@@ -74,6 +74,14 @@ static inline uint64_t gx_uop(uint32_t handler, uint32_t aux, int32_t imm) {
 }
 #endif
 
+/*
+ * Transposed event tiles: a warp's 32 records of cw words are kept as cw rows of
+ * GX_CTX_ROW(cw) words (word w of record r at w * row + r).  The padding (16 / cw words
+ * for cw = 4, 8, 16) spreads the tile's 8-byte stores over all banks; reads of one word
+ * across the warp are consecutive either way.
+ */
+#define GX_CTX_ROW(cw) (32u + (((cw) == 4u || (cw) == 8u || (cw) == 16u) ? 16u / (cw) : 0u))
+
 /* ---------------------------------------------------------------- device map descriptor */
 #define GX_SLOT_EMPTY 0u
 #define GX_SLOT_BUSY 1u

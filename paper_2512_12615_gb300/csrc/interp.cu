@@ -92,8 +92,8 @@ namespace gx {
     RC10(GXF_##OPNAME##32K, H_J32K, C, 0)           \
     case SGL(GXS_##OPNAME##32A): JUMP_TO(c32<C>(A, T)) break;
 
-/* ctx word w of this lane lives at ctxw[w * 32 + lane]; AUX is the byte offset */
-#define CTX_PTR ((const uint8_t *)(ctxw + ((AUX >> 3) << 5) + lane) + (AUX & 7))
+/* ctx word w of this lane lives at ctxw[w * env.ctx_row + lane]; AUX is the byte offset */
+#define CTX_PTR ((const uint8_t *)(ctxw + (AUX >> 3) * env.ctx_row + lane) + (AUX & 7))
 #define H_LDC(R, SZ, SG) R = load_sz<SZ, SG>(CTX_PTR); pc++;
 #define H_LDS(R, SZ, SG) R = load_sz<SZ, SG>((const uint8_t *)stack + AUX); pc++;
 #define H_LDM(R, SZ, SG) R = load_sz<SZ, SG>((const uint8_t *)B + IMM); pc++;

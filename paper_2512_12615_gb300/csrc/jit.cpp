@@ -528,8 +528,8 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             bool sign = (op & 0xE0) == 0x80;
             std::string ld = "load_sz<" + std::to_string(size) + ", " + (sign ? "true" : "false") + ">(";
             if (ii.kind == MK_CTX)
-                o << R(dst) << " = " << ld << "(const uint8_t *)(ctxw + " << ((ii.off >> 3) << 5) << " + lane) + "
-                  << (ii.off & 7) << ");";
+                o << R(dst) << " = " << ld << "(const uint8_t *)(ctxw + " << (ii.off >> 3) * GX_CTX_ROW(p.ctx_size / 8)
+                  << " + lane) + " << (ii.off & 7) << ");";
             else if (ii.kind == MK_STACK && scalar)
                 o << R(dst) << " = " << stk_load(ii.off + GX_STACK_BYTES, size, sign) << ";";
             else if (ii.kind == MK_STACK)
@@ -806,6 +806,7 @@ extern "C" int gx_jit_check(const uint64_t *insns, uint32_t n, const gx_map_spec
         jp.info = v.info;
         jp.maps.assign(maps, maps + n_maps);
         jp.use = v.map_use;
+        jp.ctx_size = opts->ctx_size;
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
         const std::string src = gx::jit_source({&jp}, msg, rc);
         std::vector<char> cubin;
