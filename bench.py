@@ -39,6 +39,10 @@ C2_EVENTS = 64 << 20
 C1_EVENTS = 1 << 20
 C3_PAIRS = 128 << 20
 SEED = 0x6758
+# DRAM bytes (read + write) per event of the specialised page-heat kernel, from one ncu capture of
+# 16M events (profiles/gx_jit_kernel_pageheat_16M.md); traffic grows with the events streamed, so a
+# launch's traffic is this figure times its events.  Re-take it whenever that kernel changes.
+PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (544.043008e6 + 20.378112e6) / 16777216
 
 
 def peaks():
@@ -210,7 +214,10 @@ def run_headline(args, gx, torch, dist_env, jit=True):
     res = {
         "value": round(value, 1), "ms_per_step": round(ms_step, 4), "gpu_launches": reps,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": round(PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT * C2_EVENTS) if jit else None,
+                     "traffic_source": "ncu capture of 16M events scaled to the launch" if jit else None,
+                     "peak_kind": peak_kind,
                      "kernel": "gx_jit_kernel" if jit else "gx_exec_kernel", "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": round(avg_launch, 4)},
         "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept, "shards": shards},
