@@ -151,6 +151,7 @@ def run_headline(args, gx, torch, dist_env, jit=True):
     maps = [gx.Map.from_spec(ctx, s) for s in specs]
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
     block, ept, shards = prog.autotune(dev, C2_EVENTS, stream=sid)
+    variant = getattr(prog, "tuned_variant", 0)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         prog.run(dev, C2_EVENTS, stream=sid)
@@ -220,7 +221,7 @@ def run_headline(args, gx, torch, dist_env, jit=True):
                      "peak_kind": peak_kind,
                      "kernel": "gx_jit_kernel" if jit else "gx_exec_kernel", "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": round(avg_launch, 4)},
-        "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept, "shards": shards},
+        "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept, "shards": shards, "variant": variant},
         "insns_per_event": round(insns_per_event, 2),
         "Minsns_per_s": round(value * insns_per_event, 1),
     }
@@ -273,7 +274,7 @@ def run_latency(gx, torch, jit=True, pairs=None):
     ctx = gx.Context(torch.cuda.current_device())
     maps = [gx.Map.from_spec(ctx, s) for s in specs]
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
-    prog.autotune(dev, pairs, stream=sid)
+    tuned = prog.autotune(dev, pairs, stream=sid) + (prog.tuned_variant,)
     times = []
     for r in range(8):
         t = EventTimer(stream)
@@ -290,7 +291,8 @@ def run_latency(gx, torch, jit=True, pairs=None):
                        "to ringbuf",
            "Mevents_per_s": round(2 * pairs / ms / 1e3, 1), "Mpairs_per_s": round(pairs / ms / 1e3, 1),
            "kernel_ms_median": round(ms, 4), "GBps": round(nbytes / ms / 1e6, 1),
-           "hbm_frac": round(nbytes / ms / 1e6 / peak, 4), "ringbuf_bytes": len(raw), "dropped": dropped}
+           "hbm_frac": round(nbytes / ms / 1e6 / peak, 4), "ringbuf_bytes": len(raw), "dropped": dropped,
+           "launch": dict(zip(("block", "ept", "shards", "variant"), tuned))}
     prog.destroy()
     for m in maps:
         m.destroy()

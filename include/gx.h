@@ -266,7 +266,13 @@ typedef struct gx_launch {
                         for the default width) to warp-aggregate the updates that miss the cache, which
                         pays when hot values miss and costs a warp match on every miss.  Ignored by the
                         interpreter. */
+    uint32_t variant; /* specialised single programs: GX_VARIANT_WIDE (registers as the compiler likes) or
+                         GX_VARIANT_CAPPED (at most 48 registers, so five 256-thread blocks share an SM);
+                         0 = tuned/default (wide).  Ignored by the interpreter and by batches. */
+    uint32_t reserved;
 } gx_launch;
+#define GX_VARIANT_WIDE 1u
+#define GX_VARIANT_CAPPED 2u
 #define GX_SHARDS_OFF 255u
 #define GX_SHARDS_AGG 0x100u
 

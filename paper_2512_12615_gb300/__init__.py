@@ -6,5 +6,5 @@ The native library (verifier, decoder, CUDA kernels, runtime) is built in-tree b
 from .gx import (  # noqa: F401
     ANY, E_ADMISSION, E_BUDGET, E_CUDA, E_DEVICE, E_NODEV, E_TIMEOUT, E_VERIFY, E2BIG, EAGAIN, EEXIST, EINVAL,
     ENOENT, ENOMEM, EXIST, MAP_ARRAY, MAP_F_NO_DELETE, MAP_HASH, MAP_RINGBUF, NOEXIST, SHARDS_AGG, SHARDS_OFF, Batch, Context, GxError, Map, Program,
-    Server, analyze, check, exported_symbols, jit_check, lib, now, parse_records, verify,
+    Server, VARIANT_CAPPED, VARIANT_WIDE, analyze, check, exported_symbols, jit_check, lib, now, parse_records, verify,
 )

@@ -120,6 +120,7 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
                  uint64_t idx_base, int64_t *ret_out, const gx_launch &lp, cudaStream_t s) {
     uint32_t block = lp.block ? lp.block : 256, ept = lp.ept ? lp.ept : 4;
     if (block < 32 || block > GX_MAX_BLOCK || block % 32 || ept < 1 || ept > 64) return GX_EINVAL;
+    if (lp.variant > GX_VARIANT_CAPPED) return GX_EINVAL;
     uint32_t area = (uint32_t)round_up(image_bytes, 16);
     uint64_t smem = exec_smem(area, block, p->opts.ctx_size);
     uint32_t wc = 0, shard_off = 0;
@@ -152,7 +153,8 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     P.shard_off = shard_off;
     if (p->jit) {
         rc = cuda_status(jit_set_smem(p->jk, smem));
-        if (rc == GX_OK) rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s));
+        if (rc == GX_OK)
+            rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s, lp.variant == GX_VARIANT_CAPPED));
     } else {
         rc = cuda_status(launch_exec(P, (unsigned)grid, block, smem, s));
     }
@@ -171,6 +173,8 @@ int tuned_launch(gx_prog *p, uint64_t n, gx_launch *out) {
     out->ept = n >= (1ull << 24) ? 8 : 4;
     out->grid = 0;
     out->shards = 0;
+    out->variant = 0;
+    out->reserved = 0;
     return 0;
 }
 
@@ -577,7 +581,7 @@ int gx_run_batch_ex(gx_prog *p, const void *events, uint64_t n, uint64_t idx_bas
     if (!p || (!events && n)) return GX_EINVAL;
     if (((uintptr_t)events) & 15) return GX_EINVAL;
     if (n == 0) return GX_OK;
-    gx_launch l;
+    gx_launch l{};
     if (lp) l = *lp;
     else tuned_launch(p, n, &l);
     return launch_plain(p, (const uint8_t *)p->dmem, p->image_bytes, events, n, idx_base, ret_out, l,
@@ -620,7 +624,7 @@ int gx_run_batch_host(gx_prog *p, const void *events_host, uint64_t n, int64_t *
     for (int i = 0; i < 2; i++)
         if (!p->streams[i] && cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking) != cudaSuccess)
             return GX_E_CUDA;
-    gx_launch l;
+    gx_launch l{};
     tuned_launch(p, chunk, &l);
     int rc = GX_OK;
     for (uint64_t off = 0, k = 0; off < n; off += chunk, k++) {
@@ -669,6 +673,9 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
     std::vector<void *> clones;
     std::vector<uint64_t> clone_bytes;
     std::vector<gx_dmap> descs;
+    /* ring buffers restart from the real ring's head before every tuning launch: a ring that
+       fills up during tuning would make the configurations tried last look cheap */
+    std::vector<std::pair<void *, const void *>> rings;
     int rc = GX_OK;
     for (auto *m : p->maps) {
         void *cl = nullptr;
@@ -683,6 +690,7 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
         gx_dmap d = m->d;
         uint8_t *base = (uint8_t *)cl;
         d.ctr = (unsigned long long *)base;
+        if (m->d.type == GX_MAP_RINGBUF) rings.push_back({base, m->dmem});
         if (d.slots) d.slots = base + ((uint8_t *)m->d.slots - (uint8_t *)m->dmem);
         d.values = base + m->off_values;
         descs.push_back(d);
@@ -702,14 +710,17 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
             cudaStreamSynchronize(s);
         }
     }
-    gx_launch chosen;
+    gx_launch chosen{};
     tuned_launch(p, n, &chosen);
     if (rc == GX_OK) {
         /* policy only: the sharding choice at one shape on a smaller sample (batch planning) */
         const uint64_t sample = std::min<uint64_t>(n, policy_only ? (1ull << 21) : (1ull << 24));
         const std::vector<uint32_t> blocks = policy_only ? std::vector<uint32_t>{256} : std::vector<uint32_t>{128, 256};
         const std::vector<uint32_t> epts =
-            policy_only ? std::vector<uint32_t>{8} : std::vector<uint32_t>{1, 2, 4, 8, 16, 32, 64};
+            policy_only ? std::vector<uint32_t>{8} : std::vector<uint32_t>{2, 4, 8, 16, 32};
+        /* specialised single programs: the wide and the register-capped entry */
+        std::vector<uint32_t> variants = {0};
+        if (!policy_only && p->jit && p->jk.kernel_capped) variants = {GX_VARIANT_WIDE, GX_VARIANT_CAPPED};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -722,11 +733,18 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
             if (p->jk.wc_max_bits > 1) widths.push_back(GX_SHARDS_AGG); /* programs with a cache */
         }
         for (uint32_t b : blocks) {
-            for (uint32_t e : epts) for (uint32_t w : widths) {
-                gx_launch l = {b, e, 0, w};
+            for (uint32_t e : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
+                gx_launch l = {b, e, 0, w, v, 0};
+                auto rewind = [&] {
+                    for (auto &r : rings) cudaMemcpyAsync(r.first, r.second, 16, cudaMemcpyDeviceToDevice, s);
+                };
+                rewind();
                 if (launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s)) continue;
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 3; r++) launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s);
+                for (int r = 0; r < 3; r++) {
+                    rewind();
+                    launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s);
+                }
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
                 float ms = 0;

@@ -24,6 +24,7 @@ struct JitProgram {
 
 struct JitKernel {
     cudaKernel_t kernel = nullptr;
+    cudaKernel_t kernel_capped = nullptr; /* one program: the entry capped at 48 registers */
     std::string key;
     size_t smem_attr = 0;
     uint32_t shard_bytes = 0; /* shared memory of the block-private combining area (max over programs) */
@@ -56,7 +57,7 @@ ShardPlan plan_shards(const JitProgram &p);
 /* compile (or fetch from the caches) one kernel running progs[slot] for chunk slot `slot` */
 int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log);
 cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
-                       cudaStream_t s);
+                       cudaStream_t s, bool capped = false);
 cudaError_t jit_set_smem(JitKernel &k, size_t bytes);
 cudaError_t jit_occupancy(const JitKernel &k, int block, size_t smem, int *blocks_per_sm);
 

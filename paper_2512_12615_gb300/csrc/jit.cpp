@@ -608,6 +608,7 @@ std::string fnv_hex(const std::string &s) {
 struct Cached {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
+    cudaKernel_t kernel_capped = nullptr;
 };
 std::mutex cache_mu;
 std::map<std::string, Cached> cache;
@@ -674,20 +675,30 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
                    "  extern __shared__ __align__(16) uint8_t smem[];\n"
                    "  const ExecEnv env = stage_env_at(smem, shard_off, (u32)ch.pad, wcp);\n  " +
                    chunk_loop(i) + "\n}\n";
-    /* several programs: at most 48 registers, so five 256-thread blocks fit on an SM whatever the mix */
-    src += std::string("} // namespace gx\n\nextern \"C\" __global__ void __launch_bounds__(") +
-           (progs.size() > 1 ? "256, 5" : "256") + ") gx_jit_kernel(gx::ExecParams P) {\n"
-           "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx_chunk &ch, gx::u64 *ctx_all) {\n";
+    std::string body = "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx_chunk &ch, gx::u64 *ctx_all) {\n";
     if (progs.size() == 1) {
-        src += "    using namespace gx;\n    " + chunk_loop(0) + "\n";
+        body += "    using namespace gx;\n    " + chunk_loop(0) + "\n";
     } else {
-        src += "    extern __shared__ __align__(16) uint8_t smem_base[];\n    switch (env.slot) {\n";
+        body += "    extern __shared__ __align__(16) uint8_t smem_base[];\n    switch (env.slot) {\n";
         for (size_t i = 0; i < progs.size(); i++)
-            src += "    case " + std::to_string(i) + ": gx::gx_chunk_" + std::to_string(i) +
-                   "(ch, env.wc_bits | (env.wc_agg << 8), (gx::u32)(env.shard - smem_base), ctx_all); break;\n";
-        src += "    }\n";
+            body += "    case " + std::to_string(i) + ": gx::gx_chunk_" + std::to_string(i) +
+                    "(ch, env.wc_bits | (env.wc_agg << 8), (gx::u32)(env.shard - smem_base), ctx_all); break;\n";
+        body += "    }\n";
     }
-    src += "  },\n" + hook("init") + ",\n" + hook("flush") + ");\n}\n";
+    body += "  },\n" + hook("init") + ",\n" + hook("flush") + ");\n}\n";
+    src += "} // namespace gx\n\n";
+    /*
+     * One program: a wide entry (registers as the compiler likes) and a capped one (at most
+     * 48, five 256-thread blocks per SM); the autotuner picks.  Several programs: capped
+     * only, so one heavy program does not cut every program's occupancy.
+     */
+    if (progs.size() == 1) {
+        src += "extern \"C\" __global__ void __launch_bounds__(256) gx_jit_kernel(gx::ExecParams P) {\n" + body;
+        src += "extern \"C\" __global__ void __launch_bounds__(256, 5) gx_jit_kernel_capped(gx::ExecParams P) {\n" +
+               body;
+    } else {
+        src += "extern \"C\" __global__ void __launch_bounds__(256, 5) gx_jit_kernel(gx::ExecParams P) {\n" + body;
+    }
     return src;
 }
 
@@ -752,6 +763,7 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
         auto it = cache.find(key);
         if (it != cache.end()) {
             out.kernel = it->second.kernel;
+            out.kernel_capped = it->second.kernel_capped;
             out.key = key;
             return GX_OK;
         }
@@ -761,7 +773,8 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
     if (rc) return rc;
     Cached c;
     if (cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
-        cudaLibraryGetKernel(&c.kernel, c.lib, "gx_jit_kernel") != cudaSuccess) {
+        cudaLibraryGetKernel(&c.kernel, c.lib, "gx_jit_kernel") != cudaSuccess ||
+        (progs.size() == 1 && cudaLibraryGetKernel(&c.kernel_capped, c.lib, "gx_jit_kernel_capped") != cudaSuccess)) {
         cudaGetLastError();
         log = "jit: loading the compiled program failed";
         return GX_E_CUDA;
@@ -771,19 +784,23 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
         cache[key] = c;
     }
     out.kernel = c.kernel;
+    out.kernel_capped = c.kernel_capped;
     out.key = key;
     return GX_OK;
 }
 
 cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool capped) {
     void *args[] = {(void *)&p};
-    return cudaLaunchKernel((const void *)k.kernel, dim3(grid), dim3(block), args, smem, s);
+    const cudaKernel_t f = capped && k.kernel_capped ? k.kernel_capped : k.kernel;
+    return cudaLaunchKernel((const void *)f, dim3(grid), dim3(block), args, smem, s);
 }
 
 cudaError_t jit_set_smem(JitKernel &k, size_t bytes) {
     if (bytes <= k.smem_attr) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute((const void *)k.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && k.kernel_capped)
+        e = cudaFuncSetAttribute((const void *)k.kernel_capped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) k.smem_attr = bytes;
     return e;
 }

@@ -45,7 +45,7 @@ class ProgOpts(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("block", u32), ("ept", u32), ("grid", u32), ("shards", u32)]
+    _fields_ = [("block", u32), ("ept", u32), ("grid", u32), ("shards", u32), ("variant", u32), ("reserved", u32)]
 
 
 class Analysis(ctypes.Structure):
@@ -56,11 +56,14 @@ SHARDS_OFF = 255
 SHARDS_AGG = 0x100  # OR into a width: warp-aggregate the updates that miss the combining cache
 
 
+VARIANT_WIDE, VARIANT_CAPPED = 1, 2
+
+
 def _launch(launch) -> Optional[Launch]:
-    """(block, ept) or (block, ept, shards) -> gx_launch; 0 fields mean tuned/default."""
+    """(block, ept[, shards[, variant]]) -> gx_launch; 0 fields mean tuned/default."""
     if launch is None:
         return None
-    return Launch(launch[0], launch[1], 0, launch[2] if len(launch) > 2 else 0)
+    return Launch(launch[0], launch[1], 0, launch[2] if len(launch) > 2 else 0, launch[3] if len(launch) > 3 else 0, 0)
 
 
 class RunStats(ctypes.Structure):
@@ -342,11 +345,12 @@ class Program:
         return st
 
     def autotune(self, events, n: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
-        """Returns the chosen (block, ept, shards)."""
+        """Returns the chosen (block, ept, shards); the kernel variant is in self.tuned_variant."""
         if n is None:
             n = events.numel() * events.element_size() // self.ctx_size
         best = Launch()
         check(lib().gx_autotune(self.h, _ptr(events), n, _stream(stream), ctypes.byref(best)), "gx_autotune")
+        self.tuned_variant = best.variant
         return best.block, best.ept, best.shards
 
 

@@ -132,3 +132,14 @@ def test_map_flags_are_checked(ctx):
     with pytest.raises(gx.GxError):
         gx.Program(ctx, prog, [m], 16)
     m.destroy()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_kernel_variants(ctx, variant):
+    """The wide and the register-capped entry of a specialised program give the same results."""
+    prog, specs, cs = P.page_heat()
+    ev = gen.pageheat_events(100_003, seed=91)
+    ev["size"][::97] = 3
+    run_both(ctx, prog, specs, cs, ev, jit=True, launch=(256, 8, 0, variant))
+    prog, specs, cs = P.latency(ring_bytes=1 << 22)
+    run_both(ctx, prog, specs, cs, gen.latency_pairs(50_001, seed=92), jit=True, launch=(128, 4, 0, variant))
