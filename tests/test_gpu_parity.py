@@ -238,6 +238,32 @@ def test_host_buffer_path_matches(ctx):
     assert gm[0].hash_items() == om[0].hash_items()
 
 
+@pytest.mark.parametrize("jit", [False, True])
+@pytest.mark.parametrize("pinned_ret", [False, True])
+def test_host_buffer_path_pinned(ctx, jit, pinned_ret):
+    """Page-locked host buffers for the events and for R0 (or a pageable R0 buffer) through the
+    staged host path."""
+    import paper_2512_12615_gb300 as gx
+
+    prog, specs, cs = P.page_heat()
+    ev = gen.pageheat_events(250_001, seed=29)
+    pinned = torch.empty(ev.nbytes, dtype=torch.uint8).pin_memory()
+    pinned.numpy()[:] = ev.view(np.uint8).reshape(-1)
+    gm = gpu_maps(ctx, specs)
+    p = gx.Program(ctx, prog, gm, cs, deterministic=True, jit=jit)
+    if pinned_ret:
+        ret_t = torch.zeros(len(ev), dtype=torch.int64).pin_memory()
+        ret = ret_t.numpy()
+    else:
+        ret = np.zeros(len(ev), dtype=np.int64)
+    p.run_host(pinned.numpy().view(ev.dtype), ret)
+    om = O.maps_from_specs(specs)
+    r0_o, _ = O.run(prog, om, ev, cs, want_r0=True)
+    assert np.array_equal(ret, r0_o)
+    assert gm[0].hash_items() == om[0].hash_items()
+    assert p.status().status == 0
+
+
 def test_verify_load_rejection_raises(ctx):
     import paper_2512_12615_gb300 as gx
 
