@@ -139,13 +139,29 @@ def oracle_insns(prog, specs, cs, ev, n_sample) -> float:
     return cnt / n_sample
 
 
+# ---------------------------------------------------------------------------- ranks (weak scaling)
+def rank_seed(rank: int) -> int:
+    """Each rank streams its own batch: same recipe, its own seed (no data-path collective)."""
+    return SEED ^ rank
+
+
+def job_rate(torch, local_ms: float, world: int, units_per_rank: int, device=None):
+    """(slowest rank's time, whole-job millions of units per second): every rank processed
+    units_per_rank units, and the job took as long as its slowest rank."""
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3) / 1e6
+
+
 # ---------------------------------------------------------------------------- headline: page heat
 def run_headline(args, gx, torch, dist_env, jit=True):
     rank, world = dist_env
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
     prog_i, specs, cs = P.page_heat()
-    ev = gen.pageheat_events(C2_EVENTS, seed=SEED ^ rank)
+    ev = gen.pageheat_events(C2_EVENTS, seed=rank_seed(rank))
     dev = to_device(ev)
     ctx = gx.Context(torch.cuda.current_device())
     maps = [gx.Map.from_spec(ctx, s) for s in specs]
@@ -182,10 +198,7 @@ def run_headline(args, gx, torch, dist_env, jit=True):
     clk = clocks.stop()
     st = prog.status()
     assert st.status == 0, f"device status {st.status}"
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms, _ = job_rate(torch, total_ms, world, C2_EVENTS * reps, device="cuda")
     ms_step = total_ms / reps
     value = world * C2_EVENTS / (ms_step / 1e3) / 1e6
     avg_launch = sum(launch_ms) / len(launch_ms)
