@@ -289,6 +289,9 @@ def run_latency(gx, torch, jit=True, pairs=None):
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
     tuned = prog.autotune(dev, pairs, stream=sid) + (prog.tuned_variant,)
     times = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.25)
     for r in range(8):
         t = EventTimer(stream)
         with t:
@@ -297,6 +300,7 @@ def run_latency(gx, torch, jit=True, pairs=None):
         raw, dropped = maps[1].drain(stream=sid)
         if r >= 2:
             times.append(ms)
+    clk = clocks.stop()
     ms = float(np.median(times))
     nbytes = pairs * 64 + len(raw)
     peak, _ = peaks()
@@ -305,7 +309,8 @@ def run_latency(gx, torch, jit=True, pairs=None):
            "Mevents_per_s": round(2 * pairs / ms / 1e3, 1), "Mpairs_per_s": round(pairs / ms / 1e3, 1),
            "kernel_ms_median": round(ms, 4), "GBps": round(nbytes / ms / 1e6, 1),
            "hbm_frac": round(nbytes / ms / 1e6 / peak, 4), "ringbuf_bytes": len(raw), "dropped": dropped,
-           "launch": dict(zip(("block", "ept", "shards", "variant"), tuned))}
+           "launch": dict(zip(("block", "ept", "shards", "variant"), tuned)), "clocks": clk,
+           "kernel_ms_all": [round(t, 4) for t in times]}
     prog.destroy()
     for m in maps:
         m.destroy()

@@ -124,7 +124,7 @@ int size_of(int op) { return (op & 0x18) == 0x00 ? 4 : (op & 0x18) == 0x08 ? 2 :
 
 std::string R(int r) { return "r" + std::to_string(r); }
 
-const uint32_t WC_FULL_MAX = 4096;  /* array maps up to this many bytes get a whole private copy */
+const uint32_t WC_FULL_MAX = 8192;  /* array maps up to this many bytes get a whole private copy */
 const uint32_t WC_CACHE_MAX = 8192; /* shared bytes of one map's cache (tags + accumulators) */
 const uint32_t WC_TOTAL_MAX = 24576; /* shared bytes of one program's combining area */
 const uint32_t WC_BITS = 8;         /* widest cache: 256 entries */
