@@ -732,26 +732,43 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
             widths = {GX_SHARDS_OFF, 0};
             if (p->jk.wc_max_bits > 1) widths.push_back(GX_SHARDS_AGG); /* programs with a cache */
         }
-        for (uint32_t b : blocks) {
-            for (uint32_t e : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
-                gx_launch l = {b, e, 0, w, v, 0};
-                auto rewind = [&] {
-                    for (auto &r : rings) cudaMemcpyAsync(r.first, r.second, 16, cudaMemcpyDeviceToDevice, s);
-                };
+        auto rewind = [&] {
+            for (auto &r : rings) cudaMemcpyAsync(r.first, r.second, 16, cudaMemcpyDeviceToDevice, s);
+        };
+        /* time `reps` launches of l over m events (after one untimed launch); < 0 if it cannot launch */
+        auto timed = [&](const gx_launch &l, uint64_t m, int reps) -> float {
+            rewind();
+            if (launch_plain(p, (const uint8_t *)timg, img_bytes, events, m, 0, nullptr, l, s)) return -1.0f;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps; r++) {
                 rewind();
-                if (launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s)) continue;
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < 3; r++) {
-                    rewind();
-                    launch_plain(p, (const uint8_t *)timg, img_bytes, events, sample, 0, nullptr, l, s);
-                }
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
+                launch_plain(p, (const uint8_t *)timg, img_bytes, events, m, 0, nullptr, l, s);
+            }
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            return ms;
+        };
+        std::vector<std::pair<float, gx_launch>> ranked;
+        for (uint32_t b : blocks)
+            for (uint32_t e : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
+                const gx_launch l = {b, e, 0, w, v, 0};
+                const float ms = timed(l, sample, 3);
+                if (ms >= 0) ranked.push_back({ms, l});
+            }
+        std::stable_sort(ranked.begin(), ranked.end(),
+                         [](const std::pair<float, gx_launch> &a, const std::pair<float, gx_launch> &b) {
+                             return a.first < b.first;
+                         });
+        /* a sample smaller than the batch can rank close shapes wrongly: the best three race on it all */
+        if (!ranked.empty()) chosen = ranked[0].second;
+        if (n > sample && ranked.size() > 1) {
+            for (size_t k = 0; k < ranked.size() && k < 3; k++) {
+                const float ms = timed(ranked[k].second, n, 2);
+                if (ms >= 0 && ms < best_ms) {
                     best_ms = ms;
-                    chosen = l;
+                    chosen = ranked[k].second;
                 }
             }
         }
