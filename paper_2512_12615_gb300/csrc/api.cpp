@@ -127,9 +127,9 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     if (!shards_valid(lp.shards)) return GX_EINVAL;
     const uint32_t sh = (lp.shards == 0 && p->pref_tuned) ? p->pref_shards : lp.shards; /* the program's tuned choice */
     if (p->jit && p->jk.shard_bytes && sh != GX_SHARDS_OFF) {
-        wc = shards_param(sh, p->jk.wc_max_bits);
+        wc = shards_param(sh, wc_default_bits(p->jk));
         shard_off = (uint32_t)round_up(smem, 16);
-        smem = shard_off + p->jk.shard_bytes;
+        smem = shard_off + wc_area_bytes(p->jk, wc & 0xFFu);
     }
     int rc = ensure_smem(p->ctx, smem);
     if (rc) return rc;
@@ -714,7 +714,7 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
     tuned_launch(p, n, &chosen);
     if (rc == GX_OK) {
         /* policy only: the sharding choice at one shape on a smaller sample (batch planning) */
-        const uint64_t sample = std::min<uint64_t>(n, policy_only ? (1ull << 21) : (1ull << 24));
+        const uint64_t sample = std::min<uint64_t>(n, policy_only ? (1ull << 21) : (1ull << 26));
         const std::vector<uint32_t> blocks = policy_only ? std::vector<uint32_t>{256} : std::vector<uint32_t>{128, 256};
         const std::vector<uint32_t> epts =
             policy_only ? std::vector<uint32_t>{8} : std::vector<uint32_t>{2, 4, 8, 16, 32};
@@ -731,6 +731,7 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
         if (p->jit && p->jk.shard_bytes) {
             widths = {GX_SHARDS_OFF, 0};
             if (p->jk.wc_max_bits > 1) widths.push_back(GX_SHARDS_AGG); /* programs with a cache */
+            if (p->jk.wc_max_bits > WC_DEFAULT_BITS) widths.push_back(p->jk.wc_max_bits); /* the widest cache */
         }
         auto rewind = [&] {
             for (auto &r : rings) cudaMemcpyAsync(r.first, r.second, 16, cudaMemcpyDeviceToDevice, s);

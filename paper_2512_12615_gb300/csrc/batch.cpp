@@ -54,8 +54,22 @@ struct Item {
  * of a program whose sharding was tuned carries that choice (bit 63 of pad, the
  * ExecParams.wc_bits value in bits 32..40).
  */
+/* the cache width a gx_launch.shards value runs with (0: combining off) */
+uint32_t bits_of(uint32_t shards, uint32_t default_bits) {
+    if (shards == GX_SHARDS_OFF) return 0;
+    const uint32_t w = shards & 0xFFu;
+    return w ? w : default_bits;
+}
+
+/* the width a persistent kernel's combining area is sized for: its default chunks' and the widest per-chunk choice */
+uint32_t area_bits(const gx::JitKernel *jk, uint32_t shards, uint32_t widest_choice) {
+    if (!jk || !jk->shard_bytes) return 0;
+    return std::max(bits_of(shards, gx::wc_default_bits(*jk)), std::min(widest_choice, jk->wc_max_bits));
+}
+
 void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vector<gx_chunk> &out,
-                 const std::map<gx_prog *, uint32_t> *slots = nullptr, uint32_t pref_bits = 0) {
+                 const std::map<gx_prog *, uint32_t> *slots = nullptr, uint32_t pref_bits = 0,
+                 uint32_t alloc_bits = 0) {
     std::vector<size_t> order(items.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return items[a].n > items[b].n; });
@@ -77,6 +91,7 @@ void make_chunks(const std::vector<Item> &items, uint64_t chunk_events, std::vec
             if (pref_bits && it.prog->pref_tuned && it.prog->pref_shards) {
                 uint32_t sh = it.prog->pref_shards;
                 uint32_t wc = sh == GX_SHARDS_OFF ? 0u : shards_param(sh, pref_bits);
+                if ((wc & 0xFFu) > alloc_bits) wc = (wc & ~0xFFu) | alloc_bits; /* never wider than the area */
                 c.pad |= (1ull << 63) | ((uint64_t)wc << 32);
             }
             out.push_back(c);
@@ -111,8 +126,14 @@ struct Persist {
         dbytes = 0;
     }
 
-    /* shards: gx_launch.shards (0 = widest combining cache of the specialised kernel, GX_SHARDS_OFF = none) */
-    int build(gx_ctx *c, uint32_t blk, uint32_t image_area, uint32_t ctx_max, uint64_t chunks, uint32_t shards = 0) {
+    /*
+     * shards: gx_launch.shards of chunks that carry no choice of their own (0 = the default
+     * width, GX_SHARDS_OFF = none); alloc_bits: the widest cache any chunk may use, which
+     * sizes the combining area.
+     */
+    uint32_t alloc_bits = 0;
+    int build(gx_ctx *c, uint32_t blk, uint32_t image_area, uint32_t ctx_max, uint64_t chunks, uint32_t shards = 0,
+              uint32_t alloc_wc = 0) {
         release();
         ctx = c;
         block = blk;
@@ -120,10 +141,11 @@ struct Persist {
         max_ctx = ctx_max;
         smem = exec_smem(area, block, max_ctx);
         uint32_t wc = 0, shard_off = 0;
+        alloc_bits = area_bits(jk, shards, alloc_wc);
         if (jk && jk->shard_bytes) { /* chunks may switch combining on even when the default is off */
-            wc = shards == GX_SHARDS_OFF ? 0u : shards_param(shards, jk->wc_max_bits);
+            wc = shards == GX_SHARDS_OFF ? 0u : shards_param(shards, gx::wc_default_bits(*jk));
             shard_off = (uint32_t)round_up(smem, 16);
-            smem = shard_off + jk->shard_bytes;
+            smem = shard_off + gx::wc_area_bytes(*jk, alloc_bits);
         }
         int rc = jk ? cuda_status(jit_set_smem(*jk, smem)) : ensure_smem(c, smem);
         if (rc) return rc;
@@ -269,10 +291,18 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t 
         max_ctx = std::max(max_ctx, it.prog->opts.ctx_size);
     }
     /* the default width lets every program use its own tuned sharding */
-    const uint32_t pref = (b->jit && shards == 0) ? b->jk.wc_max_bits : 0;
-    make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr, pref);
+    const bool use_pref = b->jit && shards == 0;
+    const uint32_t dflt = b->jit ? gx::wc_default_bits(b->jk) : 0;
+    uint32_t alloc = 0;
+    if (use_pref)
+        for (auto &it : b->items)
+            if (it.prog->pref_tuned) alloc = std::max(alloc, bits_of(it.prog->pref_shards, dflt));
+    /* one kernel holds every program: a wide cache would cost all of them occupancy */
+    alloc = std::min(alloc, dflt);
     b->persist.jk = b->jit ? &b->jk : nullptr;
-    int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size(), shards);
+    make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr, use_pref ? dflt : 0,
+                area_bits(b->persist.jk, shards, alloc));
+    int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size(), shards, alloc);
     if (rc) return rc;
     unsigned nch = (unsigned)b->chunks.size();
     if (cudaMemcpy(b->persist.table(), b->chunks.data(), b->chunks.size() * sizeof(gx_chunk),
@@ -592,11 +622,17 @@ void gx_server::run() {
             if (!sl.persist.exec || area > sl.persist.area || max_ctx > sl.persist.max_ctx) {
                 cudaStreamSynchronize(sl.stream);
                 sl.persist.jk = jit ? &jk : nullptr;
+                uint32_t widest = 0; /* the registered programs' tuned widths */
+                if (jit)
+                    for (auto &kv : prog_slot)
+                        if (kv.first->pref_tuned)
+                            widest = std::max(widest, bits_of(kv.first->pref_shards, gx::wc_default_bits(jk)));
                 rc = sl.persist.build(ctx, opts.block, std::max(area, sl.persist.area),
-                                      std::max(max_ctx, sl.persist.max_ctx), cap_chunks);
+                                      std::max(max_ctx, sl.persist.max_ctx), cap_chunks, 0, widest);
             }
             std::vector<gx_chunk> table;
-            make_chunks(items, chunk_events, table, jit ? &prog_slot : nullptr, jit ? jk.wc_max_bits : 0);
+            make_chunks(items, chunk_events, table, jit ? &prog_slot : nullptr, jit ? gx::wc_default_bits(jk) : 0,
+                        sl.persist.alloc_bits);
             if (rc == GX_OK) {
                 memcpy(sl.host_table, table.data(), table.size() * sizeof(gx_chunk));
                 /* the count travels in the same pinned buffer, in the entry after the table */

@@ -629,19 +629,21 @@ __device__ __forceinline__ void wc_fill(uint8_t *area, u32 n_words, u32 wpv, u64
 }
 
 /*
- * Cache lookup for the value at `base`: the entry's accumulator words, claiming a free
- * entry if needed, or nullptr when the entry holds another value.  tags: 2^max_bits u64.
+ * Cache lookup for the value at `base` in a cache of 2^bits entries of `esize` bytes
+ * ({u64 tag, accumulators}): the entry's accumulators, claiming a free entry if needed,
+ * or nullptr when the entry holds another value.
  */
-__device__ __forceinline__ uint8_t *wc_entry(uint8_t *tags, uint8_t *acc, u32 bits, u32 stride, u64 base) {
+__device__ __forceinline__ uint8_t *wc_entry(uint8_t *cache, u32 bits, u32 esize, u64 base) {
     const u32 h = (u32)((base * 0x9E3779B97F4A7C15ull) >> (64 - bits));
-    const u32 ta = sh_addr(tags) + h * 8u;
+    uint8_t *entry = cache + (size_t)h * esize;
+    const u32 ta = sh_addr(entry);
     u64 t;
     asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(t) : "r"(ta));
     if (t == 0) {
         asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(t) : "r"(ta), "l"(0ull), "l"(base) : "memory");
         if (t == 0) t = base;
     }
-    return t == base ? acc + (size_t)h * stride : nullptr;
+    return t == base ? entry + 8 : nullptr;
 }
 
 /* device-memory form of a combined total (the block's flush) */

@@ -27,25 +27,37 @@ struct JitKernel {
     cudaKernel_t kernel_capped = nullptr; /* one program: the entry capped at 48 registers */
     std::string key;
     size_t smem_attr = 0;
-    uint32_t shard_bytes = 0; /* shared memory of the block-private combining area (max over programs) */
+    uint32_t shard_bytes = 0; /* shared memory of the block-private combining area at its widest (0: none) */
     uint32_t wc_max_bits = 0; /* widest combining cache (0: no combinable map; 1: private arrays only) */
+    uint32_t shard_bytes_for[11] = {}; /* the area's bytes when caches are 2^b entries wide (max over programs) */
 };
 
-/* the block-private combining layout of one program (shared memory, 16-byte aligned pieces) */
+/* combining-cache width when a launch leaves it to the default: 256 entries */
+const uint32_t WC_DEFAULT_BITS = 8;
+inline uint32_t wc_default_bits(const JitKernel &k) { return k.wc_max_bits < WC_DEFAULT_BITS ? k.wc_max_bits : WC_DEFAULT_BITS; }
+inline uint32_t wc_area_bytes(const JitKernel &k, uint32_t bits) { return k.shard_bytes_for[bits > 10 ? 10 : bits]; }
+
+/*
+ * The block-private combining layout of one program (shared memory): private copies of
+ * small array maps at fixed offsets, then one cache per other map whose 2^b entries of
+ * {u64 tag, accumulators} follow each other; b = min(runtime width, the cache's max), so
+ * the caches' offsets and the area's size follow the width chosen at launch.
+ */
 struct ShardMap {
     int map = -1;
     bool full = false;       /* whole private copy of an array map, else a tagged cache */
-    uint32_t tags_off = 0;   /* cache: 2^max_bits u64 tags */
-    uint32_t acc_off = 0;    /* accumulators: values laid out with the map's value stride */
+    uint32_t acc_off = 0;    /* full: offset of the copy (values laid out with the map's stride) */
     uint32_t stride = 0;     /* value stride (bytes, multiple of 8) */
     uint32_t max_bits = 0;   /* cache: log2 entries at most */
     uint32_t n_values = 0;   /* full: max_entries */
     std::vector<uint8_t> op; /* per 4-byte word of a value: UpdClass | UC_W8 */
 };
 struct ShardPlan {
-    std::vector<ShardMap> maps;
-    uint32_t bytes = 0;
+    std::vector<ShardMap> maps; /* private copies first, then caches */
+    uint32_t full_bytes = 0;    /* bytes of the private copies */
     uint32_t max_bits = 0;
+    uint32_t bytes_for[11] = {}; /* area bytes at each width */
+    uint32_t bytes_at(uint32_t bits) const;
     const ShardMap *find(int m) const {
         for (const ShardMap &s : maps)
             if (s.map == m) return &s;

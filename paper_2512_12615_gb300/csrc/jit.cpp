@@ -125,9 +125,9 @@ int size_of(int op) { return (op & 0x18) == 0x00 ? 4 : (op & 0x18) == 0x08 ? 2 :
 std::string R(int r) { return "r" + std::to_string(r); }
 
 const uint32_t WC_FULL_MAX = 8192;  /* array maps up to this many bytes get a whole private copy */
-const uint32_t WC_CACHE_MAX = 8192; /* shared bytes of one map's cache (tags + accumulators) */
-const uint32_t WC_TOTAL_MAX = 24576; /* shared bytes of one program's combining area */
-const uint32_t WC_BITS = 8;         /* widest cache: 256 entries */
+const uint32_t WC_CACHE_MAX = 24576; /* shared bytes of one map's cache (tags + accumulators) */
+const uint32_t WC_TOTAL_MAX = 32768; /* shared bytes of one program's combining area */
+const uint32_t WC_BITS = 10;        /* widest cache: 1024 entries */
 
 uint32_t up16(uint32_t v) { return (v + 15u) & ~15u; }
 
@@ -179,7 +179,9 @@ ShardPlan plan_shards(const JitProgram &p) {
     for (const InsnInfo &ii : p.info)
         if (ii.visited && ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES && ii.vmap < (int)targeted.size())
             targeted[ii.vmap] = true;
-    uint32_t off = 0;
+    /* private copies first (fixed offsets), then the caches (offsets follow the runtime width) */
+    std::vector<ShardMap> caches;
+    uint32_t off = 0, cache_max = 0;
     for (size_t m = 0; m < p.maps.size() && m < p.use.size(); m++) {
         const gx_map_spec &ms = p.maps[m];
         if (!targeted[m] || !p.use[m].combinable()) continue;
@@ -188,50 +190,75 @@ ShardPlan plan_shards(const JitProgram &p) {
         sm.map = (int)m;
         sm.stride = (ms.value_size + 7u) & ~7u;
         sm.op = p.use[m].op;
-        if (sm.stride > 256) continue; /* identities are kept as a 64-bit mask over a value's words */
-        uint64_t full_bytes = (uint64_t)ms.max_entries * sm.stride;
-        if (ms.type == GX_MAP_ARRAY && full_bytes <= WC_FULL_MAX) {
+        const uint64_t full_bytes = (uint64_t)ms.max_entries * sm.stride;
+        if (ms.type == GX_MAP_ARRAY && full_bytes <= WC_FULL_MAX && sm.stride <= 256) {
+            const uint32_t need = up16((uint32_t)full_bytes);
+            if (off + need > WC_TOTAL_MAX) continue;
             sm.full = true;
             sm.n_values = ms.max_entries;
             sm.acc_off = off;
-            uint32_t need = up16((uint32_t)full_bytes);
-            if (off + need > WC_TOTAL_MAX) continue;
             off += need;
-        } else {
+            plan.maps.push_back(sm);
+        } else if (sm.stride <= 248) { /* an entry's words (tag + value) fit the 64-bit identity mask */
             uint32_t bits = WC_BITS;
             while (bits > 2 && (1u << bits) * (8u + sm.stride) > WC_CACHE_MAX) bits--;
-            uint32_t need = up16((1u << bits) * 8u) + up16((1u << bits) * sm.stride);
-            if (off + need > WC_TOTAL_MAX) continue;
             sm.max_bits = bits;
-            sm.tags_off = off;
-            sm.acc_off = off + up16((1u << bits) * 8u);
-            off += need;
-            plan.max_bits = std::max(plan.max_bits, bits);
+            caches.push_back(sm);
         }
+    }
+    plan.full_bytes = off;
+    for (ShardMap &sm : caches) {
+        const uint32_t need = up16((1u << sm.max_bits) * (8u + sm.stride));
+        if (off + need > WC_TOTAL_MAX) continue;
+        off += need;
+        plan.max_bits = std::max(plan.max_bits, sm.max_bits);
         plan.maps.push_back(sm);
     }
-    plan.bytes = off;
     if (!plan.maps.empty() && plan.max_bits == 0) plan.max_bits = 1;
+    for (uint32_t b = 0; b <= WC_BITS; b++) plan.bytes_for[b] = plan.bytes_at(b);
     return plan;
 }
 
+/* the area's bytes when caches hold 2^min(bits, their max) entries */
+uint32_t ShardPlan::bytes_at(uint32_t bits) const {
+    uint32_t off = full_bytes;
+    for (const ShardMap &sm : maps)
+        if (!sm.full) off += up16((1u << std::min(bits, sm.max_bits)) * (8u + sm.stride));
+    return off;
+}
+
 namespace {
+
+/* C++ expression: byte offset of cache `k` (index into sp.maps) for the runtime width env.wc_bits */
+std::string cache_off(const ShardPlan &sp, size_t k) {
+    std::string e = std::to_string(sp.full_bytes) + "u";
+    for (size_t j = 0; j < k; j++) {
+        const ShardMap &sm = sp.maps[j];
+        if (sm.full) continue;
+        e += " + (((1u << (env.wc_bits < " + std::to_string(sm.max_bits) + "u ? env.wc_bits : " +
+             std::to_string(sm.max_bits) + "u)) * " + std::to_string(8 + sm.stride) + "u + 15u) & ~15u)";
+    }
+    return "(" + e + ")";
+}
+
+std::string cache_bits(const ShardMap &sm) {
+    return "(env.wc_bits < " + std::to_string(sm.max_bits) + "u ? env.wc_bits : " + std::to_string(sm.max_bits) + "u)";
+}
 
 /* block start: identities everywhere (every thread of the block calls this) */
 std::string gen_wc_init(const ShardPlan &sp, int slot) {
     std::ostringstream o;
     o << "__device__ __forceinline__ void gx_wc_init_" << slot << "(const ExecEnv &env) {\n";
-    for (const ShardMap &sm : sp.maps) {
+    for (size_t k = 0; k < sp.maps.size(); k++) {
+        const ShardMap &sm = sp.maps[k];
         const uint32_t wpv = sm.stride / 4;
         if (sm.full) {
             o << "  wc_fill(env.shard + " << sm.acc_off << ", " << sm.n_values * wpv << "u, " << wpv << "u, "
               << hex64(and_mask(sm)) << ");\n";
-        } else {
-            o << "  { const u32 b_ = env.wc_bits < " << sm.max_bits << "u ? env.wc_bits : " << sm.max_bits << "u;\n"
-              << "    for (u32 i = threadIdx.x; i < (1u << b_); i += blockDim.x) ((u64 *)(env.shard + " << sm.tags_off
-              << "))[i] = 0;\n"
-              << "    wc_fill(env.shard + " << sm.acc_off << ", (1u << b_) * " << wpv << "u, " << wpv << "u, "
-              << hex64(and_mask(sm)) << "); }\n";
+        } else { /* entries {u64 tag = 0, accumulators}: the tag's two words, then the value's */
+            const uint32_t wpe = (8 + sm.stride) / 4;
+            o << "  wc_fill(env.shard + " << cache_off(sp, k) << ", (1u << " << cache_bits(sm) << ") * " << wpe << "u, "
+              << wpe << "u, " << hex64(and_mask(sm) << 2) << ");\n";
         }
     }
     o << "}\n";
@@ -242,7 +269,8 @@ std::string gen_wc_init(const ShardPlan &sp, int slot) {
 std::string gen_wc_flush(const ShardPlan &sp, int slot) {
     std::ostringstream o;
     o << "__device__ __forceinline__ void gx_wc_flush_" << slot << "(const ExecEnv &env) {\n";
-    for (const ShardMap &sm : sp.maps) {
+    for (size_t k = 0; k < sp.maps.size(); k++) {
+        const ShardMap &sm = sp.maps[k];
         const std::string vals = "env.maps[" + std::to_string(sm.map) + "].values";
         if (sm.full) {
             o << "  for (u32 v_ = threadIdx.x; v_ < " << sm.n_values << "u; v_ += blockDim.x) {\n"
@@ -250,11 +278,12 @@ std::string gen_wc_flush(const ShardPlan &sp, int slot) {
               << "    const u64 g_ = (u64)(" << vals << " + (size_t)v_ * " << sm.stride << ");\n"
               << flush_value(sm, "a_", "g_") << "  }\n";
         } else {
-            o << "  { const u32 b_ = env.wc_bits < " << sm.max_bits << "u ? env.wc_bits : " << sm.max_bits << "u;\n"
-              << "    for (u32 e_ = threadIdx.x; e_ < (1u << b_); e_ += blockDim.x) {\n"
-              << "      const u64 g_ = ((const u64 *)(env.shard + " << sm.tags_off << "))[e_];\n"
+            const uint32_t es = 8 + sm.stride;
+            o << "  { const uint8_t *c_ = env.shard + " << cache_off(sp, k) << ";\n"
+              << "    for (u32 e_ = threadIdx.x; e_ < (1u << " << cache_bits(sm) << "); e_ += blockDim.x) {\n"
+              << "      const u64 g_ = *(const u64 *)(c_ + (size_t)e_ * " << es << ");\n"
               << "      if (!g_) continue;\n"
-              << "      const uint8_t *a_ = env.shard + " << sm.acc_off << " + (size_t)e_ * " << sm.stride << ";\n"
+              << "      const uint8_t *a_ = c_ + (size_t)e_ * " << es << " + 8;\n"
               << flush_value(sm, "a_", "g_") << "    } }\n";
         }
     }
@@ -269,6 +298,7 @@ std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, 
                          ", __activemask());";
     const ShardMap *sm = ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES ? sp.find(ii.vmap) : nullptr;
     if (!sm) return global;
+    const size_t k = (size_t)(sm - sp.maps.data());
     std::ostringstream o;
     std::string t = std::string("<") + op + ", " + std::to_string(size) + ">";
     o << "if (env.wc_bits) { const u64 a_ = " << addr << "; ";
@@ -276,9 +306,8 @@ std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, 
         o << "sh_update" << t << "(sh_addr(env.shard + " << sm->acc_off << ") + (u32)(a_ - (u64)env.maps[" << sm->map
           << "].values), " << val << "); ";
     } else {
-        o << "const u32 b_ = env.wc_bits < " << sm->max_bits << "u ? env.wc_bits : " << sm->max_bits << "u; "
-          << "uint8_t *e_ = wc_entry(env.shard + " << sm->tags_off << ", env.shard + " << sm->acc_off << ", b_, "
-          << sm->stride << "u, a_ - " << ii.voff << "ull); "
+        o << "uint8_t *e_ = wc_entry(env.shard + " << cache_off(sp, k) << ", " << cache_bits(*sm) << ", "
+          << 8 + sm->stride << "u, a_ - " << ii.voff << "ull); "
           << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); "
           << "else if (env.wc_agg) agg_update" << t << "(a_, " << val << ", __activemask()); "
           << "else plain_atomic" << t << "((void *)a_, " << val << "); ";
@@ -752,11 +781,13 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
     if (rc) return rc;
     out.shard_bytes = 0;
     out.wc_max_bits = 0;
+    for (uint32_t &b : out.shard_bytes_for) b = 0;
     for (const JitProgram *p : progs) {
         const ShardPlan sp = plan_shards(*p);
-        out.shard_bytes = std::max(out.shard_bytes, sp.bytes);
         out.wc_max_bits = std::max(out.wc_max_bits, sp.max_bits);
+        for (uint32_t b = 0; b <= WC_BITS; b++) out.shard_bytes_for[b] = std::max(out.shard_bytes_for[b], sp.bytes_for[b]);
     }
+    out.shard_bytes = out.shard_bytes_for[WC_BITS];
     const std::string key = jit_key(src);
     {
         std::lock_guard<std::mutex> g(cache_mu);
