@@ -42,7 +42,7 @@ SEED = 0x6758
 # DRAM bytes (read + write) per event of the specialised page-heat kernel, from one ncu capture of
 # 16M events (profiles/gx_jit_kernel_pageheat_16M.md); traffic grows with the events streamed, so a
 # launch's traffic is this figure times its events.  Re-take it whenever that kernel changes.
-PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (544.043008e6 + 20.378112e6) / 16777216
+PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (543.458048e6 + 11.761152e6) / 16777216
 
 
 def peaks():

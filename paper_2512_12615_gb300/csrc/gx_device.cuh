@@ -690,18 +690,7 @@ __device__ __forceinline__ ExecEnv stage_env_at(uint8_t *smem, u32 shard_off, u3
 }
 
 __device__ __forceinline__ ExecEnv stage_env(uint8_t *smem, const ExecParams &P, u32 slot, u32 wcp) {
-    const gx_dprog_hdr *hdr = (const gx_dprog_hdr *)smem;
-    ExecEnv env;
-    env.maps = (const gx_dmap *)(smem + sizeof(gx_dprog_hdr));
-    env.uops = (const u64 *)(smem + sizeof(gx_dprog_hdr) + hdr->n_maps * sizeof(gx_dmap));
-    env.stats = hdr->stats;
-    env.budget = hdr->budget;
-    env.slot = slot;
-    env.wc_bits = wcp & 0xFFu;
-    env.wc_agg = (wcp >> 8) & 1u;
-    env.ctx_row = GX_CTX_ROW(hdr->ctx_size / 8);
-    env.shard = smem + P.shard_off;
-    return env;
+    return stage_env_at(smem, P.shard_off, slot, wcp);
 }
 
 /*
