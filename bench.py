@@ -60,7 +60,8 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem,"
+              "temperature.memory")
 
     def __init__(self, index: int) -> None:
         self.index = index
@@ -95,8 +96,11 @@ class ClockSampler:
         sm = sorted(float(s[1]) for s in busy if s[1].replace(".", "").isdigit())
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for s in busy for k in range(4) if s[6 + k].strip() in ("Active", "1")})
+        mem = sorted(float(s[10]) for s in busy if len(s) > 10 and s[10].replace(".", "").isdigit())
+        temp = sorted(float(s[11]) for s in busy if len(s) > 11 and s[11].replace(".", "").isdigit())
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": float(busy[0][2]) if busy[0][2] else None,
-                "reasons": reasons, "samples": len(busy)}
+                "reasons": reasons, "samples": len(busy), "mem_mhz": mem[len(mem) // 2] if mem else None,
+                "mem_temp_c_max": temp[-1] if temp else None}
 
 
 # ---------------------------------------------------------------------------- helpers
