@@ -208,6 +208,8 @@ ShardPlan plan_shards(const JitProgram &p) {
     }
     plan.full_bytes = off;
     for (ShardMap &sm : caches) {
+        /* narrow a cache that does not fit the program's area at its widest (down to 16 entries) */
+        while (sm.max_bits > 4 && off + up16((1u << sm.max_bits) * (8u + sm.stride)) > WC_TOTAL_MAX) sm.max_bits--;
         const uint32_t need = up16((1u << sm.max_bits) * (8u + sm.stride));
         if (off + need > WC_TOTAL_MAX) continue;
         off += need;

@@ -4,7 +4,7 @@ Block-private combining (the per-SM shards merged into the global map, Sec. 5.3)
 invisible when the program never observes a map's values: every access must be a
 non-fetching commutative update (ADD / OR / AND / XOR atomics, the atomic max / min
 helpers) at a constant offset, with one operation per 4-byte word.  Each test below
-changes one thing about the access and checks the verdict.
+changes one thing about the access and checks the outcome.
 """
 import pytest
 

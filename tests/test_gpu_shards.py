@@ -224,3 +224,13 @@ def test_autotune_reports_a_width(ctx):
     assert block in (128, 256) and 1 <= ept <= 64 and shards in (0, AGG, OFF, 10)
     # tuning ran on scratch copies: the real maps are untouched
     assert len(gm[0].hash_items()) == 0 and not gm[1].array_values().any()
+
+
+@pytest.mark.parametrize("shards", [0, 10, 4 | AGG])
+def test_three_caches_and_a_copy(ctx, shards):
+    """Four combinable maps in one program: a private array copy and three caches whose offsets
+    depend on the launch's width (the widest narrowed so that the area fits)."""
+    from tests.test_jit_compile import MANY, MANY_SPECS
+
+    ev = np.random.default_rng(5).integers(0, 2**63, size=(40_009, 4), dtype=np.uint64)
+    run_both(ctx, assemble(MANY).prog(), MANY_SPECS, 32, ev, jit=True, launch=(256, 4, shards))

@@ -26,3 +26,58 @@ def test_batch_programs_compile(p):
 def test_rejected_program_is_not_compiled():
     rc, log = gx.jit_check(assemble(["ldx8 r0 r10 -8", "exit"]).prog(), [], 16)
     assert rc == gx.E_VERIFY and "uninitialised stack" in log
+
+
+# ---------------------------------------------------------------- combining layouts (compile only)
+def _hash_upd(m, ks, vs, key_expr, body):
+    """lookup-or-insert in hash map m (key in r7 after key_expr), then body on r0 (non-NULL)"""
+    ins = [f"mov r7 {key_expr[0]}", f"and r7 {key_expr[1]}", f"stx{ks} r10 -8 r7", f"ld_map r1 {m}", "mov r2 r10",
+           "add r2 -8", "call map_lookup_elem", f"jne r0 0 have{m}"]
+    ins += [f"st8 r10 {-8 - 8 * (k + 1)} 0" for k in range(vs // 8)]
+    ins += [f"ld_map r1 {m}", "mov r2 r10", "add r2 -8", "mov r3 r10", f"add r3 {-8 - vs}", "mov r4 1",
+            "call map_update_elem", f"ld_map r1 {m}", "mov r2 r10", "add r2 -8", "call map_lookup_elem",
+            f"jeq r0 0 out{m}", f"have{m}:"] + body + [f"out{m}:"]
+    return ins
+
+
+def _arr_upd(m, n, body):
+    return ["mov r7 r8", f"and r7 {n - 1}", "stx4 r10 -4 r7", f"ld_map r1 {m}", "mov r2 r10", "add r2 -4",
+            "call map_lookup_elem", f"jeq r0 0 aout{m}"] + body + [f"aout{m}:"]
+
+
+MANY = (["mov r6 r1", "ldx8 r8 r6 8"]
+        + _hash_upd(0, 8, 24, ("r8", "0xFF"), ["mov r9 r0", "mov r1 r8", "atomic8 add r0 0 r1", "mov r1 r9",
+                                                  "add r1 8", "mov r2 r8", "call atomic_max_u64", "mov r0 r9",
+                                                  "mov r1 r8", "atomic4 xor r0 16 r1", "atomic4 or r0 20 r1"])
+        + _hash_upd(1, 8, 248, ("r8", "0x3F"), ["mov r9 r0", "mov r1 r8", "atomic8 add r0 0 r1", "mov r1 r9",
+                                                   "add r1 240", "mov r2 r8", "call atomic_min_u64"])
+        + _arr_upd(2, 16, ["mov r1 r8", "atomic8 and r0 0 r1"])
+        + _arr_upd(3, 1024, ["mov r1 r8", "atomic8 or r0 0 r1", "atomic4 add r0 8 r1"])
+        + ["mov r0 0", "exit"])
+MANY_SPECS = [dict(type=1, key_size=8, value_size=24, max_entries=512, flags=1),
+              dict(type=1, key_size=8, value_size=248, max_entries=128),
+              dict(type=2, key_size=4, value_size=8, max_entries=16),
+              dict(type=2, key_size=4, value_size=16, max_entries=1024)]  # 16 KiB: above the copy limit, cached
+
+
+def test_many_maps_compile_and_combine():
+    prog = assemble(MANY).prog()
+    rc, info, log = gx.analyze(prog, MANY_SPECS, 32, deterministic=True)
+    assert rc == 0, log
+    assert info.combinable_maps == 0b1111
+    _check(prog, MANY_SPECS, 32)
+
+
+def test_stack_at_varying_offsets_compiles():
+    # one store reaches two stack slots on different paths: the stack stays in memory
+    lines = ["ldx8 r2 r1 0", "mov r3 r10", "add r3 -8", "jeq r2 0 a", "mov r3 r10", "add r3 -16", "a:",
+             "st8 r3 0 7", "st8 r10 -8 1", "st8 r10 -16 2", "ldx8 r0 r10 -8", "exit"]
+    prog = assemble(lines).prog()
+    assert gx.verify(prog, [], 16)[0] == 0
+    _check(prog, [], 16, det=False)
+
+
+def test_ring_output_from_scalar_stack_compiles():
+    lines = ["ldx8 r2 r1 0", "stx8 r10 -16 r2", "st8 r10 -8 5", "ld_map r1 0", "mov r2 r10", "add r2 -16",
+             "mov r3 16", "mov r4 0", "call ringbuf_output", "mov r0 0", "exit"]
+    _check(assemble(lines).prog(), [dict(type=27, key_size=0, value_size=0, max_entries=4096)], 16, det=False)
