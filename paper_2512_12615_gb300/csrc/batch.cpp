@@ -622,11 +622,13 @@ void gx_server::run() {
             if (!sl.persist.exec || area > sl.persist.area || max_ctx > sl.persist.max_ctx) {
                 cudaStreamSynchronize(sl.stream);
                 sl.persist.jk = jit ? &jk : nullptr;
-                uint32_t widest = 0; /* the registered programs' tuned widths */
+                /* the registered programs' tuned widths, at most the default: one kernel holds them all */
+                uint32_t widest = 0;
                 if (jit)
                     for (auto &kv : prog_slot)
                         if (kv.first->pref_tuned)
                             widest = std::max(widest, bits_of(kv.first->pref_shards, gx::wc_default_bits(jk)));
+                if (jit) widest = std::min(widest, gx::wc_default_bits(jk));
                 rc = sl.persist.build(ctx, opts.block, std::max(area, sl.persist.area),
                                       std::max(max_ctx, sl.persist.max_ctx), cap_chunks, 0, widest);
             }
