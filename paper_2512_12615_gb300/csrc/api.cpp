@@ -775,7 +775,6 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        p->launches -= 0; /* tuning launches are counted like any other */
         if (!policy_only) p->tuned[63 - __builtin_clzll(n | 1)] = chosen;
         p->pref_shards = chosen.shards;
         p->pref_tuned = true;
