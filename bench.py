@@ -43,6 +43,8 @@ SEED = 0x6758
 # 16M events (profiles/gx_jit_kernel_pageheat_16M.md); traffic grows with the events streamed, so a
 # launch's traffic is this figure times its events.  Re-take it whenever that kernel changes.
 PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (543.458048e6 + 11.761152e6) / 16777216
+PAGEHEAT_WORKLOAD = ("page-heat policy, 64M events/GPU, Zipf(1.1) 4 KiB pages over 64 GiB, "
+                     "hash map 1M entries (u64 -> {count, last_ts}), 8-trip loop")
 
 
 def peaks():
@@ -461,8 +463,8 @@ def reference_arm(args, rank, world):
     line = {"metric": "page-heat throughput", "value": round(value, 3), "unit": "Mevents/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "page-heat, Zipf(1.1) pages over 64 GiB, hash map 1M entries",
-                       "events_per_step": n_sample, "sample_of": C2_EVENTS},
+            "config": {"workload": PAGEHEAT_WORKLOAD, "events_per_gpu": C2_EVENTS, "ctx_bytes": 32,
+                       "sample_events_per_step": n_sample},
             "cpu_baseline": {"value": round(value, 3), "unit": "Mevents/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {n_sample} events of the 64M-event page-heat batch per step"},
             "e2e": {"value": round(value, 3), "unit": "Mevents/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -553,8 +555,7 @@ def main() -> int:
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
                 "data": "synthetic", "exec": "jit (load-time specialised program; interpreter under configs)",
-                "config": {"workload": "page-heat policy, 64M events/GPU, Zipf(1.1) 4 KiB pages over 64 GiB, "
-                                       "hash map 1M entries (u64 -> {count, last_ts}), 8-trip loop",
+                "config": {"workload": PAGEHEAT_WORKLOAD,
                            "events_per_gpu": C2_EVENTS, "ctx_bytes": 32, "l2": "inputs 2 GiB per step > 129 MB L2",
                            "launch": head["launch_shape"], "maps": "resident across steps"},
                 "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"], "clocks": head["clocks"],
