@@ -307,9 +307,14 @@ typedef struct gx_run_stats {
 int gx_last_status(gx_prog *prog, gx_run_stats *out, int reset, void *stream);
 
 /*
- * Pick block size and events per thread for (prog, n) by timing candidate shapes on a
- * scratch copy of the program's maps (the real maps are not touched).  The choice is
- * cached per program and size bucket and used by later runs; *best (nullable) gets it.
+ * Pick the launch for (prog, n) by timing candidates on a scratch copy of the program's
+ * maps (the real maps, ring buffers included, are not touched): block size, events per
+ * thread and, for specialised programs, the map-sharding width and miss policy
+ * (gx_launch.shards) and the kernel variant.  Candidates are ranked on the first 64M
+ * events; when n is larger the best three are timed again on all n events.  The choice is
+ * cached per program and size bucket and used by later runs, and its sharding choice is
+ * the program's default in batches and served ticks; *best (nullable) gets it.
+ * Synchronous; GX_EINVAL for n == 0 or a null events_dev.
  */
 int gx_autotune(gx_prog *prog, const void *events_dev, uint64_t n, void *stream, gx_launch *best);
 
@@ -318,7 +323,9 @@ int gx_autotune(gx_prog *prog, const void *events_dev, uint64_t n, void *stream,
  * A batch is a fixed set of (program, events, n) items run by ONE persistent kernel:
  * blocks claim chunks of events from an atomic cursor, switch programs by restaging the
  * decoded program into shared memory, and the whole launch (cursor reset + kernel) is
- * captured once into a CUDA graph.
+ * captured once into a CUDA graph.  When every item's program is specialised, the kernel
+ * holds all of them; each chunk carries its program's tuned map sharding (at most the
+ * default width, so that one program does not cost all of them occupancy).
  */
 int gx_batch_create(gx_ctx *ctx, gx_batch **out);
 /* Add an item; ret_out_dev nullable.  Items may share programs and maps. */
