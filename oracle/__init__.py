@@ -8,6 +8,11 @@ A batch run follows the plain definition: events in index order, one program exe
 per event on a fresh register file and stack, maps and ring buffers carried over between
 events (the device handlers of Sec. 4.3 / Sec. 5.3 executed one after another; instruction
 semantics from the standard eBPF ISA, RFC 9669).
+
+`run_warps` is the warp-level form of Sec. 4.4.1 / Sec. 4.4.2: groups of up to 32
+consecutive events run one handler in lockstep, lane-varying values may not decide control
+flow or reach shared state, and side effects happen once per warp.  It reports where the
+lanes would disagree (EDIVERGE), which is what a SIMT-aware verifier must rule out.
 """
 from __future__ import annotations
 
@@ -26,6 +31,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 
 MAP_HASH, MAP_ARRAY, MAP_RINGBUF = 1, 2, 27
 ENOENT, E2BIG, EAGAIN, ENOMEM, EFAULT, EEXIST, EINVAL, EBUDGET = -2, -7, -11, -12, -14, -17, -22, -1002
+EDIVERGE = -1003  # run_warps: the lanes of a warp disagree where they must agree
 
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
@@ -68,15 +74,20 @@ def lib() -> ctypes.CDLL:
             L.or_run.argtypes = [vp, u32, vp, u32, vp, u64, u32, u64, vp, ctypes.POINTER(u64), u64,
                                  ctypes.POINTER(u64)]
             L.or_run.restype = i32
+            L.or_run_warps.argtypes = [vp, u32, vp, u32, vp, u64, u32, vp, u32, u64, vp, ctypes.POINTER(u64), u64,
+                                       ctypes.POINTER(u64), ctypes.POINTER(u32)]
+            L.or_run_warps.restype = i32
             _lib = L
     return _lib
 
 
 class OracleError(RuntimeError):
-    def __init__(self, rc: int, event: int) -> None:
-        super().__init__(f"oracle run failed rc={rc} at event {event}")
+    def __init__(self, rc: int, event: int, pc: Optional[int] = None) -> None:
+        where = f" at event {event}" + ("" if pc is None else f", insn {pc}")
+        super().__init__(f"oracle run failed rc={rc}{where}")
         self.rc = rc
         self.event = event
+        self.pc = pc
 
 
 class Map:
@@ -174,6 +185,36 @@ def run(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_size: int
                       ctypes.byref(bad))
     if rc != 0:
         raise OracleError(rc, int(bad.value))
+    return r0, int(count.value)
+
+
+def run_warps(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_size: int, *,
+              uniform: Optional[np.ndarray] = None, lanes: int = 32, event_idx_base: int = 0, want_r0: bool = False,
+              budget: int = 0) -> Tuple[Optional[np.ndarray], int]:
+    """Run `prog` over `events` as warps of `lanes` consecutive events in lockstep.
+
+    uniform: ctx_size booleans marking the warp-uniform ctx bytes (every lane of a warp must
+    carry the same value there).  Returns (R0 per event or None, instructions per warp
+    summed); raises OracleError (rc EDIVERGE where the lanes disagree, with the insn)."""
+    prog = np.ascontiguousarray(prog, dtype=np.uint64)
+    raw = np.ascontiguousarray(events).view(np.uint8).reshape(-1)
+    assert raw.size % ctx_size == 0
+    n = raw.size // ctx_size
+    uni = None
+    if uniform is not None:
+        uni = np.ascontiguousarray(np.asarray(uniform, dtype=bool).astype(np.uint8))
+        assert uni.size == ctx_size
+    handles = (ctypes.c_void_p * max(1, len(maps)))(*[m.h for m in maps])
+    r0 = np.zeros(n, dtype=np.int64) if want_r0 else None
+    count = ctypes.c_uint64(0)
+    bad = ctypes.c_uint64(0)
+    pc = ctypes.c_uint32(0)
+    rc = lib().or_run_warps(prog.ctypes.data, prog.size, handles, len(maps), raw.ctypes.data, n, ctx_size,
+                            None if uni is None else uni.ctypes.data, lanes, event_idx_base,
+                            None if r0 is None else r0.ctypes.data, ctypes.byref(count), budget, ctypes.byref(bad),
+                            ctypes.byref(pc))
+    if rc != 0:
+        raise OracleError(rc, int(bad.value), int(pc.value))
     return r0, int(count.value)
 
 

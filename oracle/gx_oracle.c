@@ -465,6 +465,7 @@ typedef struct {
     uint32_t n_maps;
     uint64_t event_idx;
     regions *g;
+    region granted; /* the region the last helper call granted (size 0: none) */
 } hctx;
 
 static or_map *map_arg(const hctx *h, uint64_t v) {
@@ -503,7 +504,7 @@ static int rb_finish(const hctx *h, uint64_t p, int discard) {
     return OR_EFAULT;
 }
 
-static int helper(const hctx *h, int32_t id, uint64_t *R) {
+static int helper(hctx *h, int32_t id, uint64_t *R) {
     regions *g = h->g;
     uint64_t r0 = 0;
     switch (id) {
@@ -513,7 +514,10 @@ static int helper(const hctx *h, int32_t id, uint64_t *R) {
         uint8_t *k = check(g, R[2], m->key_size, 0);
         if (!k) return OR_EFAULT;
         uint8_t *v = map_lookup(m, k);
-        if (v) grant(g, v, m->value_size, 1);
+        if (v) {
+            grant(g, v, m->value_size, 1);
+            h->granted = g->r[g->n - 1];
+        }
         r0 = (uint64_t)(uintptr_t)v;
         break;
     }
@@ -563,7 +567,10 @@ static int helper(const hctx *h, int32_t id, uint64_t *R) {
         or_map *m = map_arg(h, R[1]);
         if (!m || m->type != MAP_RINGBUF) return OR_EFAULT;
         uint8_t *p = R[3] ? NULL : rb_reserve(m, R[2], h->event_idx);
-        if (p) grant(g, p, R[2], 1);
+        if (p) {
+            grant(g, p, R[2], 1);
+            h->granted = g->r[g->n - 1];
+        }
         r0 = (uint64_t)(uintptr_t)p;
         break;
     }
@@ -588,7 +595,111 @@ static int helper(const hctx *h, int32_t id, uint64_t *R) {
     return OR_OK;
 }
 
-/* one event; returns OR_OK and sets *ret, or an error */
+
+/* ------------------------------------------------------------------ one instruction, one lane */
+/* ALU / ALU64 (RFC 9669 Sec. 4.1, byte swaps Sec. 4.2) on register file R */
+static int ins_alu(uint64_t *R, uint8_t op, int dst, int src, int16_t off, int32_t imm) {
+    int is32 = (op & 7) == 4;
+    uint8_t code = op & 0xF0;
+    if (dst == 10) return OR_EINVAL;
+    if (code == 0xD0) { /* END */
+        if (imm != 16 && imm != 32 && imm != 64) return OR_EINVAL;
+        if (!is32 && (op & 0x08)) return OR_EINVAL;
+        if (is32 && !(op & 0x08)) R[dst] = imm == 64 ? R[dst] : (R[dst] & ((1ULL << imm) - 1ULL));
+        else R[dst] = bswap(R[dst], imm);
+        return OR_OK;
+    }
+    uint64_t s;
+    if (op & 0x08) s = R[src];
+    else s = is32 ? (uint64_t)(uint32_t)imm : (uint64_t)(int64_t)imm;
+    if (code == 0x80 && (op & 0x08)) return OR_EINVAL;
+    if (code == 0xB0 && off != 0 && !(op & 0x08)) return OR_EINVAL;
+    uint64_t r;
+    if (alu(code, is32, off, R[dst], s, &r) != OR_OK) return OR_EINVAL;
+    R[dst] = r;
+    return OR_OK;
+}
+
+/* outcome of a conditional jump (JMP / JMP32 other than JA, CALL and EXIT; RFC 9669 Sec. 4.3) */
+static int ins_cond(const uint64_t *R, uint8_t op, int dst, int src, int32_t imm, int *taken) {
+    uint64_t s = (op & 0x08) ? R[src] : (uint64_t)(int64_t)imm;
+    return cond(op & 0xF0, (op & 7) == 6, R[dst], s, taken);
+}
+
+/* 64-bit immediate load (RFC 9669 Sec. 5.4): a constant or a map handle */
+static int ins_ld64(uint64_t *R, const hctx *h, const uint64_t *insns, uint32_t n, uint32_t pc) {
+    uint64_t w = insns[pc];
+    int dst = (int)((w >> 8) & 0xF), src = (int)((w >> 12) & 0xF);
+    int32_t imm = (int32_t)(uint32_t)(w >> 32);
+    if ((w & 0xFF) != 0x18 || pc + 1 >= n || dst == 10) return OR_EINVAL;
+    uint64_t hi = insns[pc + 1] >> 32;
+    if (src == 0) {
+        R[dst] = ((uint64_t)(uint32_t)imm) | (hi << 32);
+    } else if (src == 1) {
+        if ((uint32_t)imm >= h->n_maps) return OR_EINVAL;
+        R[dst] = (uint64_t)(uintptr_t)h->maps[(uint32_t)imm];
+    } else {
+        return OR_EINVAL;
+    }
+    return OR_OK;
+}
+
+/* LDX: MEM and MEMSX loads (RFC 9669 Sec. 5.1, 5.2) */
+static int ins_ldx(uint64_t *R, const regions *g, uint8_t op, int dst, int src, int16_t off) {
+    uint8_t mode = op & 0xE0;
+    int sz = size_of(op);
+    if (dst == 10 || (mode != 0x60 && mode != 0x80) || (mode == 0x80 && sz == 8)) return OR_EINVAL;
+    uint8_t *p = check(g, R[src] + (uint64_t)(int64_t)off, (uint64_t)sz, 0);
+    if (!p) return OR_EFAULT;
+    uint64_t v = load_le(p, sz);
+    R[dst] = mode == 0x80 ? sext(v, 8 * sz) : v;
+    return OR_OK;
+}
+
+/* the address a ST / STX writes */
+static uint64_t store_addr(const uint64_t *R, int dst, int16_t off) { return R[dst] + (uint64_t)(int64_t)off; }
+
+/* ST / STX: plain stores (RFC 9669 Sec. 5.1) and atomics (Sec. 5.3) */
+static int ins_store(uint64_t *R, const regions *g, uint8_t op, int dst, int src, int16_t off, int32_t imm) {
+    uint8_t cls = op & 7, mode = op & 0xE0;
+    int sz = size_of(op);
+    uint64_t a = store_addr(R, dst, off);
+    if (mode == 0x60) {
+        uint8_t *p = check(g, a, (uint64_t)sz, 1);
+        if (!p) return OR_EFAULT;
+        store_le(p, sz, cls == 2 ? (uint64_t)(int64_t)imm : R[src]);
+        return OR_OK;
+    }
+    if (mode != 0xC0 || cls != 3 || (sz != 4 && sz != 8)) return OR_EINVAL;
+    uint8_t *p = check(g, a, (uint64_t)sz, 1);
+    if (!p) return OR_EFAULT;
+    uint64_t mask = sz == 4 ? 0xFFFFFFFFULL : ~0ULL;
+    uint64_t old = load_le(p, sz);
+    uint64_t v = R[src] & mask;
+    int fetch = imm & 1;
+    switch (imm & ~1) {
+    case 0x00: store_le(p, sz, (old + v) & mask); break;
+    case 0x40: store_le(p, sz, old | v); break;
+    case 0x50: store_le(p, sz, old & v); break;
+    case 0xA0: store_le(p, sz, old ^ v); break;
+    case 0xE0: /* XCHG */
+        if (!fetch) return OR_EINVAL;
+        store_le(p, sz, v);
+        break;
+    case 0xF0: /* CMPXCHG */
+        if (!fetch) return OR_EINVAL;
+        if (old == (R[0] & mask)) store_le(p, sz, v);
+        R[0] = old;
+        fetch = 0;
+        break;
+    default: return OR_EINVAL;
+    }
+    if (fetch) R[src] = old;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ one event */
+/* returns OR_OK and sets *ret, or an error */
 static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uint32_t ctx_size, uint64_t budget,
                    uint64_t *ret, uint64_t *count) {
     uint64_t R[11];
@@ -614,30 +725,13 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
         int32_t imm = (int32_t)(uint32_t)(w >> 32);
         uint8_t cls = op & 7;
         uint32_t next = pc + 1;
+        int rc = OR_OK;
         if (dst > 10 || src > 10) return OR_EINVAL;
         switch (cls) {
-        case 4:   /* ALU */
-        case 7: { /* ALU64 */
-            int is32 = cls == 4;
-            uint8_t code = op & 0xF0;
-            if (dst == 10) return OR_EINVAL;
-            if (code == 0xD0) { /* END */
-                if (imm != 16 && imm != 32 && imm != 64) return OR_EINVAL;
-                if (!is32 && (op & 0x08)) return OR_EINVAL;
-                if (is32 && !(op & 0x08)) R[dst] = imm == 64 ? R[dst] : (R[dst] & ((1ULL << imm) - 1ULL));
-                else R[dst] = bswap(R[dst], imm);
-                break;
-            }
-            uint64_t s;
-            if (op & 0x08) s = R[src];
-            else s = is32 ? (uint64_t)(uint32_t)imm : (uint64_t)(int64_t)imm;
-            if (code == 0x80 && (op & 0x08)) return OR_EINVAL;
-            if (code == 0xB0 && off != 0 && !(op & 0x08)) return OR_EINVAL;
-            uint64_t r;
-            if (alu(code, is32, off, R[dst], s, &r) != OR_OK) return OR_EINVAL;
-            R[dst] = r;
+        case 4: /* ALU */
+        case 7: /* ALU64 */
+            rc = ins_alu(R, op, dst, src, off, imm);
             break;
-        }
         case 5:   /* JMP */
         case 6: { /* JMP32 */
             uint8_t code = op & 0xF0;
@@ -647,8 +741,7 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
             }
             if (code == 0x80 && cls == 5) { /* CALL */
                 if (src != 0) return OR_EINVAL;
-                int rc = helper(h, imm, R);
-                if (rc != OR_OK) return rc;
+                rc = helper(h, imm, R);
                 break;
             }
             if (code == 0x90 && cls == 5) { /* EXIT */
@@ -656,76 +749,25 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
                 *count += steps;
                 return OR_OK;
             }
-            uint64_t s = (op & 0x08) ? R[src] : (uint64_t)(int64_t)imm;
             int taken;
-            if (cond(code, cls == 6, R[dst], s, &taken) != OR_OK) return OR_EINVAL;
+            if (ins_cond(R, op, dst, src, imm, &taken) != OR_OK) return OR_EINVAL;
             if (taken) next = (uint32_t)((int64_t)pc + 1 + off);
             break;
         }
-        case 0: { /* LD: only the 64-bit immediate form */
-            if (op != 0x18 || pc + 1 >= n || dst == 10) return OR_EINVAL;
-            uint64_t hi = insns[pc + 1] >> 32;
-            if (src == 0) {
-                R[dst] = ((uint64_t)(uint32_t)imm) | (hi << 32);
-            } else if (src == 1) {
-                if ((uint32_t)imm >= h->n_maps) return OR_EINVAL;
-                R[dst] = (uint64_t)(uintptr_t)h->maps[(uint32_t)imm];
-            } else {
-                return OR_EINVAL;
-            }
+        case 0: /* LD: only the 64-bit immediate form */
+            rc = ins_ld64(R, h, insns, n, pc);
             next = pc + 2;
             break;
-        }
-        case 1: { /* LDX */
-            uint8_t mode = op & 0xE0;
-            int sz = size_of(op);
-            if (dst == 10 || (mode != 0x60 && mode != 0x80) || (mode == 0x80 && sz == 8)) return OR_EINVAL;
-            uint8_t *p = check(&g, R[src] + (uint64_t)(int64_t)off, (uint64_t)sz, 0);
-            if (!p) return OR_EFAULT;
-            uint64_t v = load_le(p, sz);
-            R[dst] = mode == 0x80 ? sext(v, 8 * sz) : v;
+        case 1: /* LDX */
+            rc = ins_ldx(R, &g, op, dst, src, off);
             break;
-        }
-        case 2:   /* ST */
-        case 3: { /* STX */
-            uint8_t mode = op & 0xE0;
-            int sz = size_of(op);
-            uint64_t a = R[dst] + (uint64_t)(int64_t)off;
-            if (mode == 0x60) {
-                uint8_t *p = check(&g, a, (uint64_t)sz, 1);
-                if (!p) return OR_EFAULT;
-                store_le(p, sz, cls == 2 ? (uint64_t)(int64_t)imm : R[src]);
-                break;
-            }
-            if (mode != 0xC0 || cls != 3 || (sz != 4 && sz != 8)) return OR_EINVAL;
-            uint8_t *p = check(&g, a, (uint64_t)sz, 1);
-            if (!p) return OR_EFAULT;
-            uint64_t mask = sz == 4 ? 0xFFFFFFFFULL : ~0ULL;
-            uint64_t old = load_le(p, sz);
-            uint64_t v = R[src] & mask;
-            int fetch = imm & 1;
-            switch (imm & ~1) {
-            case 0x00: store_le(p, sz, (old + v) & mask); break;
-            case 0x40: store_le(p, sz, old | v); break;
-            case 0x50: store_le(p, sz, old & v); break;
-            case 0xA0: store_le(p, sz, old ^ v); break;
-            case 0xE0: /* XCHG */
-                if (!fetch) return OR_EINVAL;
-                store_le(p, sz, v);
-                break;
-            case 0xF0: /* CMPXCHG */
-                if (!fetch) return OR_EINVAL;
-                if (old == (R[0] & mask)) store_le(p, sz, v);
-                R[0] = old;
-                fetch = 0;
-                break;
-            default: return OR_EINVAL;
-            }
-            if (fetch) R[src] = old;
+        case 2: /* ST */
+        case 3: /* STX */
+            rc = ins_store(R, &g, op, dst, src, off, imm);
             break;
-        }
         default: return OR_EINVAL;
         }
+        if (rc != OR_OK) return rc;
         pc = next;
     }
 }
@@ -740,6 +782,7 @@ int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_ma
            uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out, uint64_t *insn_count,
            uint64_t budget, uint64_t *bad_event) {
     hctx h;
+    memset(&h, 0, sizeof h);
     h.maps = maps;
     h.n_maps = n_maps;
     uint64_t count = 0;
@@ -758,4 +801,300 @@ int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_ma
     }
     if (insn_count) *insn_count = count;
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------ one warp, in lockstep */
+/*
+ * The warp-level execution of device handlers (Sec. 4.4.1, Sec. 4.4.2): the lanes of a
+ * warp run the handler together.  Values may differ between lanes, but they may not
+ * decide control flow or reach state outside the warp; the warp's side effects happen
+ * once, and their results reach every lane.  This is that definition written out: the
+ * lanes step in lockstep, and wherever they must agree the run checks that they do.
+ * A disagreement stops the run with OR_EDIVERGE at that instruction.
+ *
+ * Per lane: registers, a 512-byte stack, its own ctx record.  Shared: maps and rings.
+ *   - ALU, 64-bit immediates, loads, and stores and atomics on the lane's own stack:
+ *     every lane on its own.
+ *   - Conditional jumps: every lane evaluates; all must agree.
+ *   - Stores and atomics elsewhere (map values, ring-buffer records): every lane names
+ *     the same address and operand (and R0 for CMPXCHG); the leader executes it once
+ *     and a fetched old value goes to every lane.
+ *   - Warp helpers (GX_HELPER_WARP_*, 0x10010..0x10015) reduce R1 over the warp's lanes
+ *     into every lane's R0: sum mod 2^64, unsigned max, unsigned min, OR, AND, and the
+ *     number of lanes with R1 != 0.
+ *   - Other helpers: every argument the helper reads must agree (a pointer into the
+ *     lane's own stack or ctx compares by its offset there), and so must the bytes
+ *     behind a key, value or payload pointer; the leader calls it once, and R0 and any
+ *     region it grants go to every lane.  Atomic max / min on the lane's own stack runs
+ *     per lane.
+ *   - EXIT: every lane's R0 must agree.
+ * The leader is the warp's first lane: ring-buffer records carry its event index.
+ */
+#define OR_EDIVERGE (-1003)
+#define WARP_MAX 32
+
+typedef struct {
+    uint64_t R[11];
+    uint8_t stack[STACK_BYTES];
+    regions g;
+    uint8_t *ctx;
+} lane;
+
+/* a register value as every lane would see it: pointers into the lane's own stack or ctx by offset */
+static void lane_norm(const lane *l, uint32_t ctx_size, uint64_t v, int *kind, uint64_t *x) {
+    uint64_t sb = (uint64_t)(uintptr_t)l->stack, cb = (uint64_t)(uintptr_t)l->ctx;
+    if (v >= sb && v - sb <= STACK_BYTES) {
+        *kind = 1;
+        *x = v - sb;
+    } else if (v >= cb && v - cb <= ctx_size) {
+        *kind = 2;
+        *x = v - cb;
+    } else {
+        *kind = 0;
+        *x = v;
+    }
+}
+
+static int lanes_agree_reg(const lane *L, uint32_t nl, uint32_t ctx_size, int r) {
+    int k0, k;
+    uint64_t x0, x;
+    lane_norm(&L[0], ctx_size, L[0].R[r], &k0, &x0);
+    for (uint32_t i = 1; i < nl; i++) {
+        lane_norm(&L[i], ctx_size, L[i].R[r], &k, &x);
+        if (k != k0 || x != x0) return 0;
+    }
+    return 1;
+}
+
+/* the `size` bytes at each lane's R[r] are readable and the same in every lane; -1 unreadable */
+static int lanes_agree_bytes(const lane *L, uint32_t nl, int r, uint64_t size) {
+    const uint8_t *p0 = check(&L[0].g, L[0].R[r], size, 0);
+    if (!p0) return -1;
+    for (uint32_t i = 1; i < nl; i++) {
+        const uint8_t *p = check(&L[i].g, L[i].R[r], size, 0);
+        if (!p) return -1;
+        if (memcmp(p, p0, size)) return 0;
+    }
+    return 1;
+}
+
+static int in_own_stack(const lane *l, uint64_t a) {
+    uint64_t sb = (uint64_t)(uintptr_t)l->stack;
+    return a >= sb && a - sb < STACK_BYTES;
+}
+
+static int helper_nargs(int32_t id) {
+    switch (id) {
+    case 1: case 3: case 132: case 133: case 0x10000: case 0x10001: return 2;
+    case 2: case 130: return 4;
+    case 131: return 3;
+    }
+    return 0;
+}
+
+/* a helper call by the whole warp */
+static int warp_call(hctx *h, lane *L, uint32_t nl, uint32_t ctx_size, int32_t id) {
+    if (id >= 0x10010 && id <= 0x10015) { /* warp helpers: a reduction over the lanes */
+        uint64_t acc = id == 0x10012 || id == 0x10014 ? ~0ULL : 0;
+        for (uint32_t i = 0; i < nl; i++) {
+            uint64_t v = L[i].R[1];
+            switch (id) {
+            case 0x10010: acc += v; break;
+            case 0x10011: if (v > acc) acc = v; break;
+            case 0x10012: if (v < acc) acc = v; break;
+            case 0x10013: acc |= v; break;
+            case 0x10014: acc &= v; break;
+            case 0x10015: acc += v != 0; break;
+            }
+        }
+        for (uint32_t i = 0; i < nl; i++) {
+            L[i].R[0] = acc;
+            for (int r = 1; r <= 5; r++) L[i].R[r] = 0;
+        }
+        return OR_OK;
+    }
+    if ((id == 0x10000 || id == 0x10001) && in_own_stack(&L[0], L[0].R[1])) { /* lane-private memory */
+        for (uint32_t i = 0; i < nl; i++) {
+            if (!in_own_stack(&L[i], L[i].R[1])) return OR_EDIVERGE;
+            h->g = &L[i].g;
+            int rc = helper(h, id, L[i].R);
+            if (rc != OR_OK) return rc;
+        }
+        return OR_OK;
+    }
+    for (int r = 1; r <= helper_nargs(id); r++)
+        if (!lanes_agree_reg(L, nl, ctx_size, r)) return OR_EDIVERGE;
+    or_map *m = map_arg(h, L[0].R[1]);
+    if (m && m->type != MAP_RINGBUF && (id == 1 || id == 2 || id == 3)) {
+        int a = lanes_agree_bytes(L, nl, 2, m->key_size);
+        if (a == 1 && id == 2) a = lanes_agree_bytes(L, nl, 3, m->value_size);
+        if (a < 0) return OR_EFAULT;
+        if (a == 0) return OR_EDIVERGE;
+    }
+    if (m && m->type == MAP_RINGBUF && id == 130 && L[0].R[3] <= 4096) {
+        int a = lanes_agree_bytes(L, nl, 2, L[0].R[3]);
+        if (a < 0) return OR_EFAULT;
+        if (a == 0) return OR_EDIVERGE;
+    }
+    h->g = &L[0].g;
+    h->granted.size = 0;
+    int rc = helper(h, id, L[0].R);
+    if (rc != OR_OK) return rc;
+    for (uint32_t i = 1; i < nl; i++) {
+        if (h->granted.size) grant(&L[i].g, h->granted.base, h->granted.size, h->granted.writable);
+        L[i].R[0] = L[0].R[0];
+        for (int r = 1; r <= 5; r++) L[i].R[r] = 0;
+    }
+    return OR_OK;
+}
+
+/* a store or atomic by the whole warp */
+static int warp_store(lane *L, uint32_t nl, uint8_t op, int dst, int src, int16_t off, int32_t imm) {
+    uint8_t cls = op & 7, mode = op & 0xE0;
+    int own = in_own_stack(&L[0], store_addr(L[0].R, dst, off));
+    for (uint32_t i = 1; i < nl; i++)
+        if (in_own_stack(&L[i], store_addr(L[i].R, dst, off)) != own) return OR_EDIVERGE;
+    if (own) {
+        for (uint32_t i = 0; i < nl; i++) {
+            int rc = ins_store(L[i].R, &L[i].g, op, dst, src, off, imm);
+            if (rc != OR_OK) return rc;
+        }
+        return OR_OK;
+    }
+    /* outside the lanes' stacks: one address, one operand, executed once */
+    uint64_t a = store_addr(L[0].R, dst, off);
+    int cmpx = mode == 0xC0 && imm == 0xF1;
+    for (uint32_t i = 1; i < nl; i++) {
+        if (store_addr(L[i].R, dst, off) != a) return OR_EDIVERGE;
+        if (cls == 3 && L[i].R[src] != L[0].R[src]) return OR_EDIVERGE;
+        if (cmpx && L[i].R[0] != L[0].R[0]) return OR_EDIVERGE;
+        if (!check(&L[i].g, a, (uint64_t)size_of(op), 1)) return OR_EFAULT;
+    }
+    int rc = ins_store(L[0].R, &L[0].g, op, dst, src, off, imm);
+    if (rc != OR_OK) return rc;
+    if (mode == 0xC0)
+        for (uint32_t i = 1; i < nl; i++) {
+            if (cmpx) L[i].R[0] = L[0].R[0];
+            else if (imm & 1) L[i].R[src] = L[0].R[src];
+        }
+    return OR_OK;
+}
+
+static int run_warp(const uint64_t *insns, uint32_t n, hctx *h, lane *L, uint32_t nl, uint32_t ctx_size,
+                    uint64_t budget, uint64_t *ret, uint64_t *count, uint32_t *bad_pc) {
+    for (uint32_t i = 0; i < nl; i++) {
+        memset(L[i].R, 0, sizeof L[i].R);
+        memset(L[i].stack, 0, sizeof L[i].stack);
+        L[i].g.n = 0;
+        grant(&L[i].g, L[i].ctx, ctx_size, 0);
+        grant(&L[i].g, L[i].stack, STACK_BYTES, 1);
+        L[i].R[1] = (uint64_t)(uintptr_t)L[i].ctx;
+        L[i].R[10] = (uint64_t)(uintptr_t)(L[i].stack + STACK_BYTES);
+    }
+    uint64_t steps = 0;
+    uint32_t pc = 0;
+    for (;;) {
+        *bad_pc = pc;
+        if (pc >= n) return OR_EFAULT;
+        if (++steps > budget) return OR_EBUDGET;
+        uint64_t w = insns[pc];
+        uint8_t op = (uint8_t)(w & 0xFF);
+        int dst = (int)((w >> 8) & 0xF), src = (int)((w >> 12) & 0xF);
+        int16_t off = (int16_t)(uint16_t)((w >> 16) & 0xFFFF);
+        int32_t imm = (int32_t)(uint32_t)(w >> 32);
+        uint8_t cls = op & 7;
+        uint32_t next = pc + 1;
+        int rc = OR_OK;
+        if (dst > 10 || src > 10) return OR_EINVAL;
+        switch (cls) {
+        case 4:
+        case 7:
+            for (uint32_t i = 0; i < nl && rc == OR_OK; i++) rc = ins_alu(L[i].R, op, dst, src, off, imm);
+            break;
+        case 5:
+        case 6: {
+            uint8_t code = op & 0xF0;
+            if (code == 0x00) {
+                next = (uint32_t)((int64_t)pc + 1 + (cls == 6 ? imm : off));
+                break;
+            }
+            if (code == 0x80 && cls == 5) {
+                if (src != 0) return OR_EINVAL;
+                rc = warp_call(h, L, nl, ctx_size, imm);
+                break;
+            }
+            if (code == 0x90 && cls == 5) {
+                for (uint32_t i = 1; i < nl; i++)
+                    if (L[i].R[0] != L[0].R[0]) return OR_EDIVERGE;
+                for (uint32_t i = 0; i < nl; i++) ret[i] = L[i].R[0];
+                *count += steps;
+                return OR_OK;
+            }
+            int t0 = 0, t;
+            for (uint32_t i = 0; i < nl; i++) {
+                if (ins_cond(L[i].R, op, dst, src, imm, &t) != OR_OK) return OR_EINVAL;
+                if (i == 0) t0 = t;
+                else if (t != t0) return OR_EDIVERGE;
+            }
+            if (t0) next = (uint32_t)((int64_t)pc + 1 + off);
+            break;
+        }
+        case 0:
+            for (uint32_t i = 0; i < nl && rc == OR_OK; i++) rc = ins_ld64(L[i].R, h, insns, n, pc);
+            next = pc + 2;
+            break;
+        case 1:
+            for (uint32_t i = 0; i < nl && rc == OR_OK; i++) rc = ins_ldx(L[i].R, &L[i].g, op, dst, src, off);
+            break;
+        case 2:
+        case 3:
+            rc = warp_store(L, nl, op, dst, src, off, imm);
+            break;
+        default: return OR_EINVAL;
+        }
+        if (rc != OR_OK) return rc;
+        pc = next;
+    }
+}
+
+/*
+ * Run the program over n_events records as warps of `lanes` consecutive events (1..32;
+ * the last warp may be shorter), one warp after another (see run_warp above).  uniform
+ * (nullable): ctx_size flags, nonzero marking a warp-uniform ctx byte; every lane of a
+ * warp must carry the same value there (else OR_EINVAL for that warp).  r0_out, insn_count
+ * (instructions per warp, summed), budget: as or_run.  Returns 0 or the first error with
+ * *bad_event = the first event of the failing warp and *bad_pc = the instruction.
+ */
+int or_run_warps(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
+                 uint64_t n_events, uint32_t ctx_size, const uint8_t *uniform, uint32_t lanes, uint64_t event_idx_base,
+                 int64_t *r0_out, uint64_t *insn_count, uint64_t budget, uint64_t *bad_event, uint32_t *bad_pc) {
+    if (lanes < 1 || lanes > WARP_MAX) return OR_EINVAL;
+    lane *L = (lane *)calloc(WARP_MAX, sizeof(lane));
+    if (!L) return OR_ENOMEM;
+    hctx h;
+    memset(&h, 0, sizeof h);
+    h.maps = maps;
+    h.n_maps = n_maps;
+    uint64_t count = 0, ret[WARP_MAX];
+    uint32_t pc = 0;
+    if (budget == 0) budget = 1ULL << 20;
+    int rc = OR_OK;
+    for (uint64_t w0 = 0; w0 < n_events && rc == OR_OK; w0 += lanes) {
+        uint32_t nl = (uint32_t)(n_events - w0 < lanes ? n_events - w0 : lanes);
+        for (uint32_t i = 0; i < nl; i++) L[i].ctx = (uint8_t *)(uintptr_t)(events + (w0 + i) * (uint64_t)ctx_size);
+        for (uint32_t b = 0; uniform && b < ctx_size && rc == OR_OK; b++)
+            for (uint32_t i = 1; uniform[b] && i < nl; i++)
+                if (L[i].ctx[b] != L[0].ctx[b]) rc = OR_EINVAL;
+        h.event_idx = event_idx_base + w0;
+        if (rc == OR_OK) rc = run_warp(insns, n_insns, &h, L, nl, ctx_size, budget, ret, &count, &pc);
+        if (rc != OR_OK) {
+            if (bad_event) *bad_event = w0;
+            if (bad_pc) *bad_pc = pc;
+        } else if (r0_out) {
+            for (uint32_t i = 0; i < nl; i++) r0_out[w0 + i] = (int64_t)ret[i];
+        }
+    }
+    free(L);
+    if (insn_count) *insn_count = count;
+    return rc;
 }

@@ -52,6 +52,13 @@ HELPER = {
     "ringbuf_discard": 133,
     "atomic_max_u64": 0x10000,
     "atomic_min_u64": 0x10001,
+    # warp-level aggregation (SIMT verification only): u64 (u64 v) reduced over the warp's lanes
+    "warp_sum_u64": 0x10010,
+    "warp_max_u64": 0x10011,
+    "warp_min_u64": 0x10012,
+    "warp_or_u64": 0x10013,
+    "warp_and_u64": 0x10014,
+    "warp_count": 0x10015,
 }
 BPF_ANY, BPF_NOEXIST, BPF_EXIST = 0, 1, 2
 PSEUDO_MAP_FD = 1
