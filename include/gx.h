@@ -86,6 +86,18 @@ extern "C" {
 #define GX_HELPER_RINGBUF_DISCARD 133
 #define GX_HELPER_ATOMIC_MAX_U64 0x10000 /* void (u64 *p, u64 v): *p = max(*p, v) */
 #define GX_HELPER_ATOMIC_MIN_U64 0x10001 /* void (u64 *p, u64 v): *p = min(*p, v) */
+/*
+ * Warp-level aggregation (Sec. 4.4.1: lane-varying values reach control flow or shared
+ * state only through a warp-level reduction): u64 (u64 v) reduced over the warp's lanes,
+ * the same result in every lane.  Accepted only by gx_verify_simt; the per-lane engine
+ * (gx_verify / gx_verify_load) rejects them as unknown helpers.
+ */
+#define GX_HELPER_WARP_SUM_U64 0x10010 /* sum mod 2^64 */
+#define GX_HELPER_WARP_MAX_U64 0x10011 /* unsigned maximum */
+#define GX_HELPER_WARP_MIN_U64 0x10012 /* unsigned minimum */
+#define GX_HELPER_WARP_OR_U64 0x10013
+#define GX_HELPER_WARP_AND_U64 0x10014
+#define GX_HELPER_WARP_COUNT 0x10015 /* number of lanes with v != 0 */
 
 /* limits */
 #define GX_MAX_INSNS 4096
@@ -246,6 +258,65 @@ typedef struct gx_analysis {
 } gx_analysis;
 int gx_analyze(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
                const gx_prog_opts *opts, gx_analysis *out, char *log, size_t log_len);
+/*
+ * SIMT-aware verification (host only, no device needed): the warp-uniformity pass and
+ * per-hook resource budgets of Sec. 4.4.1 and Sec. 5.3, run together with the ordinary
+ * checks of gx_verify.  The program is read as a warp-level handler: the lanes of a warp
+ * run it in lockstep, each lane with its own ctx record, registers and stack, and shared
+ * state changes once per warp.  A value is lane-varying when it derives from a ctx byte
+ * that `uniform` does not mark (the role the paper gives BTF annotations), from a
+ * lane-varying value, or from lane-varying stack bytes; constants, map handles, the ctx
+ * and stack pointers, helper results and values loaded through a uniform pointer are
+ * warp-uniform.  Rejected, with the instruction and a GX_SIMT_V_* reason:
+ *   GX_SIMT_V_BRANCH  a conditional jump (so also a loop bound) on a lane-varying value;
+ *   GX_SIMT_V_KEY     a lane-varying key for lookup, update or delete;
+ *   GX_SIMT_V_ATOMIC  an atomic on map memory (BPF_ATOMIC or the max / min helpers) with a
+ *                     lane-varying address or operand;
+ *   GX_SIMT_V_STORE   a store into map or ring-buffer memory with a lane-varying address
+ *                     or value;
+ *   GX_SIMT_V_HELPER  another lane-varying helper argument (update value, ring-buffer
+ *                     payload, flags);
+ *   GX_SIMT_V_RET     a lane-varying R0 at exit (the decision broadcast to the lanes);
+ *   GX_SIMT_V_INSNS / _HELPERS / _MEM  a path over the instruction, helper-call or
+ *                     memory-operation budget;
+ *   GX_SIMT_V_VERIFY  an ordinary verification failure (the log says which).
+ * Lane-varying values reach these places only through GX_HELPER_WARP_* reductions.  The
+ * helper set has no barrier or grid-wide synchronisation, and unknown helpers are refused.
+ * Returns 0 if accepted, GX_E_VERIFY if rejected, GX_EINVAL for bad arguments; `out`
+ * (nullable) is filled either way.
+ */
+typedef struct gx_simt_spec {
+    const uint8_t *uniform;    /* opts->ctx_size flags, nonzero = warp-uniform ctx byte; NULL = none */
+    uint32_t max_insns;        /* budget per path: instructions executed (a 64-bit immediate counts once);
+                                  0 = unlimited */
+    uint32_t max_helper_calls; /* budget per path: helper calls; 0 = unlimited */
+    uint32_t max_mem_ops;      /* budget per path: loads, stores and atomics; 0 = unlimited */
+    uint32_t reserved;         /* 0 */
+} gx_simt_spec;
+typedef struct gx_simt_report {
+    uint64_t max_insns;        /* the most instructions on any path explored */
+    uint32_t max_helper_calls; /* the most helper calls on any path */
+    uint32_t max_mem_ops;      /* the most loads, stores and atomics on any path */
+    uint32_t uniform_branches; /* conditional jumps with an open outcome, all on uniform values */
+    uint32_t varying_insns;    /* instructions that compute a lane-varying value (lane-local work) */
+    int32_t violation_pc;      /* the rejected instruction; -1 if accepted */
+    uint32_t violation;        /* GX_SIMT_V_* */
+} gx_simt_report;
+#define GX_SIMT_V_NONE 0u
+#define GX_SIMT_V_VERIFY 1u
+#define GX_SIMT_V_BRANCH 2u
+#define GX_SIMT_V_KEY 3u
+#define GX_SIMT_V_ATOMIC 4u
+#define GX_SIMT_V_STORE 5u
+#define GX_SIMT_V_HELPER 6u
+#define GX_SIMT_V_RET 7u
+#define GX_SIMT_V_INSNS 8u
+#define GX_SIMT_V_HELPERS 9u
+#define GX_SIMT_V_MEM 10u
+int gx_verify_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+                   const gx_prog_opts *opts, const gx_simt_spec *simt, gx_simt_report *out, char *log,
+                   size_t log_len);
+
 /* Verify, decode and upload a program; it holds a reference on each map. */
 int gx_verify_load(gx_ctx *ctx, const uint64_t *insns, uint32_t n_insns, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len);

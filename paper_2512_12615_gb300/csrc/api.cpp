@@ -479,6 +479,44 @@ int gx_analyze(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint3
     return rc;
 }
 
+int gx_verify_simt(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                   const gx_prog_opts *opts, const gx_simt_spec *simt, gx_simt_report *out, char *log, size_t log_len) {
+    if (out) {
+        memset(out, 0, sizeof *out);
+        out->violation_pc = -1;
+    }
+    if (!insns || !opts || !simt || (n_maps && !maps) || simt->reserved) return GX_EINVAL;
+    if (opts->ctx_size < 8 || opts->ctx_size > GX_MAX_CTX) return GX_EINVAL;
+    SimtIn in;
+    in.uniform.assign(opts->ctx_size, 0);
+    if (simt->uniform)
+        for (uint32_t b = 0; b < opts->ctx_size; b++) in.uniform[b] = simt->uniform[b] != 0;
+    in.max_insns = simt->max_insns;
+    in.max_helpers = simt->max_helper_calls;
+    in.max_mem = simt->max_mem_ops;
+    VerifyOut v;
+    int rc = verify_program(insns, n, maps, n_maps, *opts, v, &in);
+    if (rc == GX_E_VERIFY && v.simt.violation == GX_SIMT_V_NONE) {
+        v.simt.violation = GX_SIMT_V_VERIFY;
+        v.simt.pc = v.fail_pc;
+    }
+    if (out) {
+        out->max_insns = v.simt.max_insns;
+        out->max_helper_calls = v.simt.max_helpers;
+        out->max_mem_ops = v.simt.max_mem;
+        out->uniform_branches = v.simt.uniform_branches;
+        out->varying_insns = v.simt.varying_insns;
+        out->violation_pc = rc == GX_OK ? -1 : v.simt.pc;
+        out->violation = rc == GX_OK ? GX_SIMT_V_NONE : v.simt.violation;
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, v.log.size());
+        memcpy(log, v.log.data(), k);
+        log[k] = 0;
+    }
+    return rc;
+}
+
 int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len) {
     if (!c || !insns || !opts || !out || (n_maps && !maps)) return GX_EINVAL;

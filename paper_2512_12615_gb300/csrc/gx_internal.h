@@ -49,9 +49,24 @@ struct MapUse {
     }
 };
 
+/* SIMT-aware verification (gx_verify_simt): what to check and what was found */
+struct SimtIn {
+    std::vector<uint8_t> uniform; /* per ctx byte: nonzero = warp-uniform */
+    uint32_t max_insns = 0, max_helpers = 0, max_mem = 0; /* per-path budgets, 0 = unlimited */
+};
+struct SimtOut {
+    uint64_t max_insns = 0;
+    uint32_t max_helpers = 0, max_mem = 0;
+    uint32_t uniform_branches = 0, varying_insns = 0;
+    int32_t pc = -1;
+    uint32_t violation = GX_SIMT_V_NONE;
+};
+
 struct VerifyOut {
     std::vector<InsnInfo> info;
     std::string log;
+    int32_t fail_pc = -1; /* the rejected instruction */
+    SimtOut simt;
     uint64_t insns_processed = 0;
     uint64_t states_stored = 0;
     uint32_t stack_depth = 0; /* deepest stack byte touched */
@@ -60,7 +75,7 @@ struct VerifyOut {
 
 /* returns GX_OK or GX_E_VERIFY / GX_EINVAL; out.log explains a rejection */
 int verify_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
-                   const gx_prog_opts &opts, VerifyOut &out);
+                   const gx_prog_opts &opts, VerifyOut &out, const SimtIn *simt = nullptr);
 
 /* translate a verified program to micro-ops (see gx_layout.h) */
 int decode_program(const uint64_t *insns, uint32_t n, const VerifyOut &v, std::vector<uint64_t> &uops,

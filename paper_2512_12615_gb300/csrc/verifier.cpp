@@ -27,6 +27,16 @@
  *   NOEXIST inserts of constant bytes; deletes, XCHG and CMPXCHG on map memory are
  *   refused.  Under these rules the final map state, the set of ring-buffer records and
  *   every R0 are the same for every order in which the events run.
+ *   SIMT mode (gx_verify_simt; the warp-uniformity pass and per-hook budgets of Sec. 4.4.1
+ *   and Sec. 5.3): a second mark, lane-varying, starts at the ctx bytes not declared
+ *   warp-uniform and flows like the taint through registers, spills and stack bytes.  A
+ *   value the abstract state pins to one constant is uniform whatever its mark: control
+ *   flow is uniform, so every lane holds that constant.  Lane-varying values may not reach
+ *   branch conditions, map keys, helper arguments, R0 at exit, or the address or operand
+ *   of a store or atomic into map or ring-buffer memory; the warp helpers turn them into
+ *   uniform values.  Each path also counts its instructions, helper calls and memory
+ *   operations against the hook's budgets; a state is pruned only by a kept state whose
+ *   counts are at least as large, so the maxima found are the maxima over all paths.
  */
 #include <stdarg.h>
 #include <stdio.h>
@@ -50,6 +60,9 @@ const int MAX_STATES_PER_PC = 64;
 const size_t MAX_STATES_TOTAL = 16384;
 
 enum RT : uint8_t { NI = 0, SC, CTX, STK, CMAP, MV, MVN, RB, RBN };
+const uint8_t ST_LV = 0x40, ST_TAINT = 0x80;
+
+
 const char *rt_name(int t) {
     static const char *n[] = {"uninit", "scalar", "ctx", "stack", "map", "map_value", "map_value_or_null",
                               "ringbuf_mem", "ringbuf_mem_or_null"};
@@ -59,6 +72,7 @@ const char *rt_name(int t) {
 struct Reg {
     uint8_t t = NI;
     uint8_t taint = 0;
+    uint8_t lv = 0; /* SIMT mode: lane-varying */
     uint8_t map = 0;
     uint8_t tz = 0; /* known zero low bits of the value (scalar) or offset (pointer) */
     u32 id = 0;     /* maybe-NULL group / ring-buffer reference */
@@ -68,11 +82,14 @@ struct Reg {
 };
 
 bool same(const Reg &a, const Reg &b) {
-    return a.t == b.t && a.taint == b.taint && a.map == b.map && a.tz == b.tz && a.id == b.id && a.size == b.size &&
+    return a.t == b.t && a.taint == b.taint && a.lv == b.lv && a.map == b.map && a.tz == b.tz && a.id == b.id && a.size == b.size &&
            a.umin == b.umin && a.umax == b.umax && a.smin == b.smin && a.smax == b.smax;
 }
 
 int ctz64(u64 v) { return v ? __builtin_ctzll(v) : 64; }
+
+/* a value that may differ between the lanes of a warp (a constant cannot) */
+bool varies(const Reg &r) { return r.lv && !(r.umin == r.umax); }
 
 Reg sc_const(u64 v) {
     Reg r;
@@ -212,11 +229,13 @@ Reg trunc32(const Reg &a) {
     if (is_const(a)) {
         Reg c = sc_const(a.umin & 0xFFFFFFFFULL);
         c.taint = a.taint;
+        c.lv = a.lv;
         return c;
     }
     Reg r = sc_range(0, 0xFFFFFFFFULL);
     r.tz = std::min<int>(a.tz, 32);
     r.taint = a.taint;
+    r.lv = a.lv;
     sync(r);
     return r;
 }
@@ -358,6 +377,7 @@ Reg abs_alu(int code, bool w32, int off, const Reg &a, const Reg &b) {
         if (!sync(r)) r = sc_range(0, 0xFFFFFFFFULL);
     }
     r.taint = a.taint | b.taint;
+    r.lv = a.lv | b.lv;
     return r;
 }
 
@@ -366,10 +386,11 @@ enum SB : uint8_t { S_INV = 0, S_MISC = 1, S_SPILL = 2 };
 
 struct State {
     Reg r[11];
-    uint8_t st[GX_STACK_BYTES]; /* SB in bits 0..1, taint in bit 7 */
+    uint8_t st[GX_STACK_BYTES]; /* SB in bits 0..1, lane-varying in bit 6, taint in bit 7 */
     Reg spill[GX_STACK_BYTES / 8];
     u32 refs[8];
     uint8_t nrefs = 0;
+    u32 c_insn = 0, c_help = 0, c_mem = 0; /* SIMT mode: this path's instructions, helper calls, memory ops */
     State() {
         memset(st, 0, sizeof st);
         memset(refs, 0, sizeof refs);
@@ -406,16 +427,44 @@ struct Verifier {
     std::vector<OpRange> op_ranges[GX_MAX_MAPS];
     u32 next_id = 1;
     char msg[512];
+    const SimtIn *simt = nullptr; /* SIMT mode when set */
+    bool sm = false;
+    std::vector<uint8_t> simt_branch, simt_vary; /* per instruction: a uniform open branch / a varying value */
 
-    int fail(u32 pc, const char *fmt, ...) __attribute__((format(printf, 3, 4))) {
-        va_list ap;
-        va_start(ap, fmt);
+    int vfail(u32 pc, const char *fmt, va_list ap) {
         vsnprintf(msg, sizeof msg, fmt, ap);
-        va_end(ap);
         char buf[640];
         snprintf(buf, sizeof buf, "insn %u: %s", pc, msg);
         out->log = buf;
+        out->fail_pc = (int32_t)pc;
         return GX_E_VERIFY;
+    }
+    int fail(u32 pc, const char *fmt, ...) __attribute__((format(printf, 3, 4))) {
+        va_list ap;
+        va_start(ap, fmt);
+        int rc = vfail(pc, fmt, ap);
+        va_end(ap);
+        return rc;
+    }
+    /* a SIMT-mode rejection with its GX_SIMT_V_* reason */
+    int sfail(u32 pc, u32 why, const char *fmt, ...) __attribute__((format(printf, 4, 5))) {
+        out->simt.violation = why;
+        out->simt.pc = (int32_t)pc;
+        va_list ap;
+        va_start(ap, fmt);
+        int rc = vfail(pc, fmt, ap);
+        va_end(ap);
+        return rc;
+    }
+    /* SIMT mode: some byte of ctx[a, a + size) is not declared warp-uniform */
+    bool ctx_varies(s64 a, int size) {
+        if (!sm) return false;
+        for (s64 b = a; b < a + size; b++)
+            if (!simt->uniform[(size_t)b]) return true;
+        return false;
+    }
+    void note_vary(u32 pc, const Reg &r) {
+        if (sm && varies(r)) simt_vary[pc] = 1;
     }
 
     /* ---------------------------------------------------- decode helpers */
@@ -444,6 +493,12 @@ struct Verifier {
         case GX_HELPER_RINGBUF_DISCARD: return 2;
         case GX_HELPER_ATOMIC_MAX_U64: return 2;
         case GX_HELPER_ATOMIC_MIN_U64: return 2;
+        case GX_HELPER_WARP_SUM_U64:
+        case GX_HELPER_WARP_MAX_U64:
+        case GX_HELPER_WARP_MIN_U64:
+        case GX_HELPER_WARP_OR_U64:
+        case GX_HELPER_WARP_AND_U64:
+        case GX_HELPER_WARP_COUNT: return sm ? 1 : -1;
         }
         return -1;
     }
@@ -580,6 +635,7 @@ struct Verifier {
         if (o.t == NI) return true;
         if (o.t != c.t) return false;
         if (c.taint && !o.taint) return false;
+        if (c.lv && !o.lv) return false;
         if (o.t == CMAP) return o.map == c.map;
         if (o.t == CTX || o.t == STK || o.t == SC || o.t == MV || o.t == MVN || o.t == RB || o.t == RBN) {
             if (o.map != c.map || o.size != c.size) return false;
@@ -599,7 +655,8 @@ struct Verifier {
         for (int b = 0; b < GX_STACK_BYTES; b++) {
             int ot = o.st[b] & 3, ct = c.st[b] & 3;
             if (ot == S_INV) continue;
-            if ((c.st[b] & 0x80) && !(o.st[b] & 0x80)) return false;
+            if ((c.st[b] & ST_TAINT) && !(o.st[b] & ST_TAINT)) return false;
+            if ((c.st[b] & ST_LV) && !(o.st[b] & ST_LV)) return false;
             if (ot == S_MISC) {
                 if (ct == S_INV) return false;
                 if (ct == S_SPILL && c.spill[b / 8].t != SC) return false;
@@ -713,13 +770,15 @@ struct Verifier {
     /* read `size` stack bytes at abs: fills *res (if non-null) */
     int stack_read(u32 pc, State &s, int abs, int size, Reg *res, bool sign) {
         int b0 = abs + GX_STACK_BYTES;
-        bool taint = false;
+        bool taint = false, lv = false;
         for (int b = b0; b < b0 + size; b++) {
             if ((s.st[b] & 3) == S_INV) return fail(pc, "read of uninitialised stack at %d", b - GX_STACK_BYTES);
             if ((s.st[b] & 3) == S_SPILL && s.spill[b / 8].t != SC && !(size == 8 && b0 % 8 == 0))
                 return fail(pc, "partial read of a spilled pointer");
-            if (s.st[b] & 0x80) taint = true;
+            if (s.st[b] & ST_TAINT) taint = true;
             if ((s.st[b] & 3) == S_SPILL && s.spill[b / 8].taint) taint = true;
+            if (s.st[b] & ST_LV) lv = true;
+            if ((s.st[b] & 3) == S_SPILL && varies(s.spill[b / 8])) lv = true;
         }
         if (!res) return GX_OK;
         if (size == 8 && b0 % 8 == 0 && (s.st[b0] & 3) == S_SPILL) {
@@ -735,10 +794,11 @@ struct Verifier {
             sync(*res);
         }
         res->taint = taint;
+        res->lv = lv;
         return GX_OK;
     }
 
-    void stack_write(State &s, int abs, int size, const Reg *val, bool taint) {
+    void stack_write(State &s, int abs, int size, const Reg *val, bool taint, bool lv) {
         int b0 = abs + GX_STACK_BYTES;
         if (size == 8 && b0 % 8 == 0 && val) {
             for (int b = b0; b < b0 + 8; b++) s.st[b] = S_SPILL;
@@ -747,17 +807,19 @@ struct Verifier {
         }
         for (int slot = b0 / 8; slot <= (b0 + size - 1) / 8; slot++) {
             if ((s.st[slot * 8] & 3) == S_SPILL) { /* breaking a spill: its bytes become plain data */
-                uint8_t t = s.spill[slot].taint ? 0x80 : 0;
+                uint8_t t = (s.spill[slot].taint ? ST_TAINT : 0) | (varies(s.spill[slot]) ? ST_LV : 0);
                 for (int b = slot * 8; b < slot * 8 + 8; b++) s.st[b] = S_MISC | t;
             }
         }
-        for (int b = b0; b < b0 + size; b++) s.st[b] = S_MISC | (taint ? 0x80 : 0);
+        for (int b = b0; b < b0 + size; b++) s.st[b] = S_MISC | (taint ? ST_TAINT : 0) | (lv ? ST_LV : 0);
     }
 
     /* helper memory argument: readable `size` bytes at p; all_const reports constant spills */
-    int mem_arg(u32 pc, State &s, const Reg &p, u64 size, const char *what, bool *tainted, bool *all_const) {
+    int mem_arg(u32 pc, State &s, const Reg &p, u64 size, const char *what, bool *tainted, bool *all_const,
+                bool *varying = nullptr) {
         if (tainted) *tainted = false;
         if (all_const) *all_const = true;
+        if (varying) *varying = p.lv != 0;
         int need = size % 8 == 0 ? 3 : size % 4 == 0 ? 2 : size % 2 == 0 ? 1 : 0;
         if (p.t == STK) {
             if (!is_const(p)) return fail(pc, "%s: variable stack offset", what);
@@ -771,8 +833,10 @@ struct Verifier {
                 int t = s.st[b] & 3;
                 if (t == S_INV) return fail(pc, "%s: uninitialised stack byte at %d", what, b - GX_STACK_BYTES);
                 if (t == S_SPILL && s.spill[b / 8].t != SC) return fail(pc, "%s: pointer spilled in the argument", what);
-                bool tb = (s.st[b] & 0x80) || (t == S_SPILL && s.spill[b / 8].taint);
+                bool tb = (s.st[b] & ST_TAINT) || (t == S_SPILL && s.spill[b / 8].taint);
                 if (tb && tainted) *tainted = true;
+                bool vb = (s.st[b] & ST_LV) || (t == S_SPILL && varies(s.spill[b / 8]));
+                if (vb && varying) *varying = true;
                 if (all_const && !(t == S_SPILL && is_const(s.spill[b / 8]) && b0 % 8 == 0 && size % 8 == 0))
                     *all_const = false;
             }
@@ -945,7 +1009,7 @@ struct Verifier {
                 if ((imm != 16 && imm != 32 && imm != 64) || src || off) return fail(pc, "invalid byte-swap");
                 if (rd(dst) || s.r[dst].t != SC) return fail(pc, "byte swap of a non-scalar");
                 Reg &d = s.r[dst];
-                uint8_t t = d.taint;
+                uint8_t t = d.taint, lv = d.lv;
                 if (is_const(d)) {
                     u64 v = d.umin;
                     v = (w32 && !x) ? (imm == 64 ? v : v & ((1ULL << imm) - 1)) : bswap_n(v, imm);
@@ -956,6 +1020,8 @@ struct Verifier {
                     d = sc_unknown();
                 }
                 d.taint = t;
+                d.lv = lv;
+                note_vary(pc, d);
                 pc++;
                 return GX_OK;
             }
@@ -991,6 +1057,7 @@ struct Verifier {
                         s.r[dst].smax = (s64)s.r[dst].umax;
                     }
                 }
+                note_vary(pc, s.r[dst]);
                 pc++;
                 return GX_OK;
             }
@@ -1004,6 +1071,7 @@ struct Verifier {
             if (code == 0x80) b = sc_const(0);
             if (a.t == SC && b.t == SC) {
                 s.r[dst] = abs_alu(code, w32, off, a, b);
+                note_vary(pc, s.r[dst]);
                 pc++;
                 return GX_OK;
             }
@@ -1049,6 +1117,7 @@ struct Verifier {
             }
             np.tz = std::min(p.tz, sk.tz);
             if (lo == hi) np.tz = (uint8_t)ctz64((u64)lo);
+            np.lv = (p.t == MV || p.t == RB) ? (uint8_t)(p.lv || varies(k)) : 0; /* ctx / stack offsets are constants */
             s.r[dst] = np;
             pc++;
             return GX_OK;
@@ -1067,6 +1136,7 @@ struct Verifier {
                 if (rd(0)) return GX_E_VERIFY;
                 if (s.r[0].t != SC) return fail(pc, "R0 at exit is a %s, not a scalar", rt_name(s.r[0].t));
                 if (det && s.r[0].taint) return fail(pc, "order-dependent value returned in R0");
+                if (sm && varies(s.r[0])) return sfail(pc, GX_SIMT_V_RET, "lane-varying value returned in R0");
                 if (s.nrefs) return fail(pc, "ring-buffer reservation neither submitted nor discarded");
                 res = STEP_DONE;
                 return GX_OK;
@@ -1087,7 +1157,9 @@ struct Verifier {
                 Reg &z = a_ptr ? b : a;
                 if (w32 || (code != 0x10 && code != 0x50) || z.t != SC || !is_const(z) || z.umin != 0)
                     return fail(pc, "pointer comparison other than a NULL check");
+                if (sm && p.lv) return sfail(pc, GX_SIMT_V_BRANCH, "NULL check of a lane-varying pointer");
                 if (p.t == MVN || p.t == RBN) {
+                    if (sm) simt_branch[pc] = 1;
                     u32 id = p.id;
                     *alt = s;
                     /* taken branch: JEQ -> NULL, JNE -> non-NULL */
@@ -1106,6 +1178,10 @@ struct Verifier {
             if (is_const(a) && is_const(b)) {
                 pc = eval_cond(code, w32, a.umin, b.umin) ? tgt : fall;
                 return GX_OK;
+            }
+            if (sm) {
+                if (varies(a) || varies(b)) return sfail(pc, GX_SIMT_V_BRANCH, "branch on a lane-varying value");
+                simt_branch[pc] = 1;
             }
             bool can_refine = !w32 || (a.umax <= 0x7FFFFFFFULL && b.umax <= 0x7FFFFFFFULL);
             State st_taken = s;
@@ -1178,6 +1254,7 @@ struct Verifier {
                 if (a < 0 || a + size > (s64)opts.ctx_size) return fail(pc, "ctx read out of bounds at %lld", (long long)a);
                 if (a % size) return fail(pc, "misaligned ctx read");
                 if (note(pc, MK_CTX, (int)a)) return GX_E_VERIFY;
+                v.lv = ctx_varies(a, size);
                 break;
             }
             case STK: {
@@ -1190,16 +1267,20 @@ struct Verifier {
             case MV:
                 if (check_range(pc, p, off, size, maps[p.map].value_size, "map value")) return GX_E_VERIFY;
                 v.taint = det ? 1 : 0;
+                v.lv = p.lv; /* one address in every lane reads one value */
                 use_other(p.map);
                 if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
                 break;
             case RB:
                 if (check_range(pc, p, off, size, p.size, "ring-buffer record")) return GX_E_VERIFY;
+                v.lv = p.lv;
                 if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
                 break;
             default: return fail(pc, "load through a %s", rt_name(p.t));
             }
             s.r[dst] = v;
+            s.c_mem++;
+            note_vary(pc, v);
             pc++;
             return GX_OK;
         }
@@ -1207,6 +1288,7 @@ struct Verifier {
             int mode = op & 0xE0, size = size_of(op);
             if (rd(dst)) return GX_E_VERIFY;
             const Reg p = s.r[dst];
+            s.c_mem++;
             if (mode == 0xC0) return atomic(s, pc, size, p, off, imm, src, cls);
             if (mode != 0x60) return fail(pc, "unsupported store mode");
             Reg v;
@@ -1225,19 +1307,24 @@ struct Verifier {
                 int abs = 0;
                 if (stack_abs(pc, p, off, size, abs)) return GX_E_VERIFY;
                 if (v.t != SC && (abs + GX_STACK_BYTES) % 8) return fail(pc, "misaligned pointer spill");
-                stack_write(s, abs, size, size == 8 ? &v : nullptr, v.taint);
+                stack_write(s, abs, size, size == 8 ? &v : nullptr, v.taint, varies(v));
                 if (note(pc, MK_STACK, abs)) return GX_E_VERIFY;
                 break;
             }
             case MV:
                 if (check_range(pc, p, off, size, maps[p.map].value_size, "map value")) return GX_E_VERIFY;
                 if (det) return fail(pc, "plain store into map memory in deterministic mode");
+                if (sm && (p.lv || varies(v)))
+                    return sfail(pc, GX_SIMT_V_STORE, "lane-varying %s stored into map memory", p.lv ? "address" : "value");
                 use_other(p.map);
                 if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
                 break;
             case RB:
                 if (check_range(pc, p, off, size, p.size, "ring-buffer record")) return GX_E_VERIFY;
                 if (det && v.taint) return fail(pc, "order-dependent value written to the ring buffer");
+                if (sm && (p.lv || varies(v)))
+                    return sfail(pc, GX_SIMT_V_STORE, "lane-varying %s stored into a ring-buffer record",
+                                 p.lv ? "address" : "value");
                 if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
                 break;
             case CTX: return fail(pc, "the ctx is read-only");
@@ -1268,6 +1355,9 @@ struct Verifier {
             if (check_range(pc, p, off, size, maps[p.map].value_size, "map value")) return GX_E_VERIFY;
             if (det && (xchg || cmpx)) return fail(pc, "exchange on map memory in deterministic mode");
             if (det && s.r[src].taint) return fail(pc, "order-dependent value added into map memory");
+            if (sm && (p.lv || varies(s.r[src]) || (cmpx && varies(s.r[0]))))
+                return sfail(pc, GX_SIMT_V_ATOMIC, "non-uniform atomic on map memory (lane-varying %s)",
+                             p.lv ? "address" : "operand");
             old.taint = det ? 1 : 0;
             if (!xchg && !cmpx) {
                 int cls = base == 0x00 ? OPC_ADD : base == 0x40 ? OPC_OR : base == 0x50 ? OPC_AND : OPC_XOR;
@@ -1287,8 +1377,10 @@ struct Verifier {
             Reg cur;
             if (stack_read(pc, s, abs, size, &cur, false)) return GX_E_VERIFY;
             old.taint = cur.taint;
+            old.lv = cur.lv;
             bool t = cur.taint || s.r[src].taint || (cmpx && s.r[0].taint);
-            stack_write(s, abs, size, nullptr, t);
+            bool lv = varies(cur) || varies(s.r[src]) || (cmpx && varies(s.r[0]));
+            stack_write(s, abs, size, nullptr, t, lv);
             note_vmap(pc, -2, -1);
             if (note(pc, MK_STACK, abs)) return GX_E_VERIFY;
         } else {
@@ -1327,13 +1419,15 @@ struct Verifier {
         };
         Reg r0 = sc_unknown();
         bool r0_void = false;
+        s.c_help++;
         switch (id) {
         case GX_HELPER_MAP_LOOKUP: {
             if (need_map(1)) return GX_E_VERIFY;
             const gx_map_spec &m = maps[s.r[1].map];
-            bool t;
-            if (mem_arg(pc, s, s.r[2], m.key_size, "lookup key", &t, nullptr)) return GX_E_VERIFY;
+            bool t, vk;
+            if (mem_arg(pc, s, s.r[2], m.key_size, "lookup key", &t, nullptr, &vk)) return GX_E_VERIFY;
             if (det && t) return fail(pc, "order-dependent map key");
+            if (sm && vk) return sfail(pc, GX_SIMT_V_KEY, "lane-varying lookup key");
             r0 = Reg();
             r0.t = MVN;
             r0.map = s.r[1].map;
@@ -1346,10 +1440,13 @@ struct Verifier {
         case GX_HELPER_MAP_UPDATE: {
             if (need_map(1)) return GX_E_VERIFY;
             const gx_map_spec &m = maps[s.r[1].map];
-            bool tk, tv, kc, vc;
-            if (mem_arg(pc, s, s.r[2], m.key_size, "update key", &tk, &kc)) return GX_E_VERIFY;
-            if (mem_arg(pc, s, s.r[3], m.value_size, "update value", &tv, &vc)) return GX_E_VERIFY;
+            bool tk, tv, kc, vc, vk, vv;
+            if (mem_arg(pc, s, s.r[2], m.key_size, "update key", &tk, &kc, &vk)) return GX_E_VERIFY;
+            if (mem_arg(pc, s, s.r[3], m.value_size, "update value", &tv, &vc, &vv)) return GX_E_VERIFY;
             if (s.r[4].t != SC) return fail(pc, "update flags must be a scalar");
+            if (sm && vk) return sfail(pc, GX_SIMT_V_KEY, "lane-varying update key");
+            if (sm && vv) return sfail(pc, GX_SIMT_V_HELPER, "lane-varying value for a map update");
+            if (sm && varies(s.r[4])) return sfail(pc, GX_SIMT_V_HELPER, "lane-varying update flags");
             if (!is_const(s.r[4]) || s.r[4].umin != GX_NOEXIST) use_other(s.r[1].map); /* may overwrite a value */
             if (det) {
                 if (tk) return fail(pc, "order-dependent map key");
@@ -1365,8 +1462,9 @@ struct Verifier {
             if (need_map(1)) return GX_E_VERIFY;
             if (det) return fail(pc, "map delete in deterministic mode");
             if (maps[s.r[1].map].flags & GX_MAP_F_NO_DELETE) return fail(pc, "map delete on a map created without deletes");
-            bool t;
-            if (mem_arg(pc, s, s.r[2], maps[s.r[1].map].key_size, "delete key", &t, nullptr)) return GX_E_VERIFY;
+            bool t, vk;
+            if (mem_arg(pc, s, s.r[2], maps[s.r[1].map].key_size, "delete key", &t, nullptr, &vk)) return GX_E_VERIFY;
+            if (sm && vk) return sfail(pc, GX_SIMT_V_KEY, "lane-varying delete key");
             r0 = sc_unknown();
             break;
         }
@@ -1374,9 +1472,10 @@ struct Verifier {
             if (need_map(2)) return GX_E_VERIFY;
             if (s.r[3].t != SC || !is_const(s.r[3]) || s.r[3].umin == 0 || s.r[3].umin > GX_MAX_VALUE)
                 return fail(pc, "ringbuf_output size must be a constant in [1, %d]", GX_MAX_VALUE);
-            bool t;
-            if (mem_arg(pc, s, s.r[2], s.r[3].umin, "ringbuf_output data", &t, nullptr)) return GX_E_VERIFY;
+            bool t, vd;
+            if (mem_arg(pc, s, s.r[2], s.r[3].umin, "ringbuf_output data", &t, nullptr, &vd)) return GX_E_VERIFY;
             if (det && t) return fail(pc, "order-dependent ring-buffer payload");
+            if (sm && vd) return sfail(pc, GX_SIMT_V_HELPER, "lane-varying ring-buffer payload");
             if (s.r[4].t != SC || !is_const(s.r[4]) || (s.r[4].umin & ~3ULL)) return fail(pc, "bad ringbuf_output flags");
             r0 = sc_unknown();
             r0.taint = det ? 1 : 0;
@@ -1405,6 +1504,7 @@ struct Verifier {
             const Reg &p = s.r[1];
             if (p.t != RB || !is_const(p) || p.umin != 0) return fail(pc, "submit/discard needs an unmodified non-NULL reservation");
             if (s.r[2].t != SC) return fail(pc, "submit/discard flags must be a scalar");
+            if (sm && (p.lv || varies(s.r[2]))) return sfail(pc, GX_SIMT_V_HELPER, "lane-varying submit/discard argument");
             release_ref(s, p.id);
             r0_void = true;
             break;
@@ -1416,12 +1516,23 @@ struct Verifier {
             if (check_range(pc, p, 0, 8, maps[p.map].value_size, "map value")) return GX_E_VERIFY;
             if (s.r[2].t != SC) return fail(pc, "atomic max/min operand must be a scalar");
             if (det && s.r[2].taint) return fail(pc, "order-dependent value folded into map memory");
+            if (sm && (p.lv || varies(s.r[2])))
+                return sfail(pc, GX_SIMT_V_ATOMIC, "non-uniform atomic max/min (lane-varying %s)", p.lv ? "address" : "operand");
             if (note_update(pc, p, 0, 8, id == GX_HELPER_ATOMIC_MAX_U64 ? OPC_MAX : OPC_MIN)) return GX_E_VERIFY;
             use_update(pc, p, 0, 8, id == GX_HELPER_ATOMIC_MAX_U64 ? UC_MAX : UC_MIN);
             r0_void = true;
             if (note(pc, MK_MEM, 0)) return GX_E_VERIFY;
             break;
         }
+        case GX_HELPER_WARP_SUM_U64:
+        case GX_HELPER_WARP_MAX_U64:
+        case GX_HELPER_WARP_MIN_U64:
+        case GX_HELPER_WARP_OR_U64:
+        case GX_HELPER_WARP_AND_U64:
+        case GX_HELPER_WARP_COUNT: /* SIMT mode only (helper_args): a reduction over the lanes, uniform */
+            if (s.r[1].t != SC) return fail(pc, "warp helper operand must be a scalar");
+            r0 = id == GX_HELPER_WARP_COUNT ? sc_range(0, 32) : sc_unknown();
+            break;
         }
         for (int i = 1; i <= 5; i++) s.r[i] = Reg();
         s.r[0] = r0_void ? Reg() : r0;
@@ -1440,6 +1551,11 @@ struct Verifier {
         if (n_maps > GX_MAX_MAPS) return fail(0, "too many maps");
         if (structure()) return GX_E_VERIFY;
         visited.assign(n, {});
+        if (sm) {
+            if (simt->uniform.size() != opts.ctx_size) return fail(0, "uniform flags must cover the %u ctx bytes", opts.ctx_size);
+            simt_branch.assign(n, 0);
+            simt_vary.assign(n, 0);
+        }
         std::vector<Pending> stack;
         {
             Pending p;
@@ -1474,6 +1590,9 @@ struct Verifier {
                                 return fail(cur.pc, "infinite loop: a state repeats exactly");
                             continue;
                         }
+                        const State &k = nodes[idx].st; /* its paths were counted from its own counts */
+                        if (sm && (cur.st.c_insn > k.c_insn || cur.st.c_help > k.c_help || cur.st.c_mem > k.c_mem))
+                            continue;
                         pruned = true;
                         break;
                     }
@@ -1486,8 +1605,25 @@ struct Verifier {
                     }
                 }
                 int res;
-                u32 alt_pc = 0;
+                u32 alt_pc = 0, at = cur.pc;
+                if (sm && simt->max_insns && ++cur.st.c_insn > simt->max_insns)
+                    return sfail(at, GX_SIMT_V_INSNS, "a path exceeds the hook budget of %u instructions", simt->max_insns);
+                if (sm && !simt->max_insns) ++cur.st.c_insn;
                 if (step(cur.st, cur.pc, &alt, &alt_pc, res)) return GX_E_VERIFY;
+                if (sm) {
+                    if (simt->max_helpers && cur.st.c_help > simt->max_helpers)
+                        return sfail(at, GX_SIMT_V_HELPERS, "a path exceeds the hook budget of %u helper calls",
+                                     simt->max_helpers);
+                    if (simt->max_mem && cur.st.c_mem > simt->max_mem)
+                        return sfail(at, GX_SIMT_V_MEM, "a path exceeds the hook budget of %u memory operations",
+                                     simt->max_mem);
+                    if (res == STEP_DONE) {
+                        SimtOut &o = out->simt;
+                        o.max_insns = std::max<u64>(o.max_insns, cur.st.c_insn);
+                        o.max_helpers = std::max(o.max_helpers, cur.st.c_help);
+                        o.max_mem = std::max(o.max_mem, cur.st.c_mem);
+                    }
+                }
                 if (res == STEP_DONE || res == STEP_PRUNE) break;
                 if (res == STEP_BRANCH) {
                     Pending p;
@@ -1498,6 +1634,12 @@ struct Verifier {
                 }
             }
         }
+        if (sm) {
+            for (u32 i = 0; i < n; i++) {
+                out->simt.uniform_branches += simt_branch[i];
+                out->simt.varying_insns += simt_vary[i];
+            }
+        }
         return GX_OK;
     }
 };
@@ -1505,7 +1647,7 @@ struct Verifier {
 } // namespace
 
 int verify_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps, const gx_prog_opts &opts,
-                   VerifyOut &out) {
+                   VerifyOut &out, const SimtIn *simt) {
     if (!insns || (n_maps && !maps)) return GX_EINVAL;
     for (uint32_t i = 0; i < n_maps; i++) {
         const gx_map_spec &m = maps[i];
@@ -1528,6 +1670,8 @@ int verify_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, u
     v.n_maps = n_maps;
     v.opts = opts;
     v.out = &out;
+    v.simt = simt;
+    v.sm = simt != nullptr;
     return v.run();
 }
 

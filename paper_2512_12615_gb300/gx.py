@@ -52,6 +52,21 @@ class Analysis(ctypes.Structure):
     _fields_ = [("insns_processed", u64), ("stack_depth", u32), ("combinable_maps", u32)]
 
 
+class SimtSpec(ctypes.Structure):
+    _fields_ = [("uniform", ctypes.c_void_p), ("max_insns", u32), ("max_helper_calls", u32), ("max_mem_ops", u32),
+                ("reserved", u32)]
+
+
+class SimtReport(ctypes.Structure):
+    _fields_ = [("max_insns", u64), ("max_helper_calls", u32), ("max_mem_ops", u32), ("uniform_branches", u32),
+                ("varying_insns", u32), ("violation_pc", i32), ("violation", u32)]
+
+
+# gx_simt_report.violation
+(SIMT_V_NONE, SIMT_V_VERIFY, SIMT_V_BRANCH, SIMT_V_KEY, SIMT_V_ATOMIC, SIMT_V_STORE, SIMT_V_HELPER, SIMT_V_RET,
+ SIMT_V_INSNS, SIMT_V_HELPERS, SIMT_V_MEM) = range(11)
+
+
 SHARDS_OFF = 255
 SHARDS_AGG = 0x100  # OR into a width: warp-aggregate the updates that miss the combining cache
 
@@ -106,6 +121,8 @@ _SIGS = {
                          ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "gx_jit_check": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                            ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_verify_simt": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                             ctypes.POINTER(SimtSpec), ctypes.POINTER(SimtReport), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
                              ctypes.POINTER(ProgOpts), ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                              ctypes.c_size_t]),
@@ -211,6 +228,28 @@ def analyze(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, determi
     log = ctypes.create_string_buffer(1024)
     rc = lib().gx_analyze(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
                           ctypes.byref(out), log, 1024)
+    return rc, out, log.value.decode()
+
+
+def verify_simt(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, uniform=None, *, max_insns: int = 0,
+                max_helper_calls: int = 0, max_mem_ops: int = 0, deterministic: bool = False,
+                insn_budget: int = 0) -> Tuple[int, SimtReport, str]:
+    """Host-only SIMT-aware verification (gx_verify_simt): (status, gx_simt_report, log).
+
+    uniform: ctx_size flags marking the warp-uniform ctx bytes (None: no byte is uniform)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    specs = _specs(map_specs)
+    opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
+    uni = None
+    if uniform is not None:
+        uni = np.ascontiguousarray(np.asarray(uniform, dtype=bool).astype(np.uint8))
+        if uni.size != ctx_size:
+            raise ValueError(f"uniform has {uni.size} flags for a {ctx_size}-byte ctx")
+    spec = SimtSpec(None if uni is None else uni.ctypes.data, max_insns, max_helper_calls, max_mem_ops, 0)
+    out = SimtReport()
+    log = ctypes.create_string_buffer(1024)
+    rc = lib().gx_verify_simt(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
+                              ctypes.byref(spec), ctypes.byref(out), log, 1024)
     return rc, out, log.value.decode()
 
 

@@ -19,6 +19,8 @@ MIRRORS = {
     "gx_server_opts": G.ServerOpts,
     "gx_completion": G.Completion,
     "gx_request": G.Request,
+    "gx_simt_spec": G.SimtSpec,
+    "gx_simt_report": G.SimtReport,
 }
 
 
