@@ -5,6 +5,7 @@ both the oracle and, at sizes the oracle cannot reach quickly, the engine:
   counting  -> bincount of event.kind
   page_heat -> group-by of addr >> 21: (sum of weights, max timestamp); per-kind tally
   latency   -> 2-D histogram of (kernel id, floor(log2(latency))); outliers latency > T
+  warp_heat -> per warp: lowest / highest region, lanes in the lowest, sizes, misaligned lanes
 """
 from __future__ import annotations
 
@@ -83,3 +84,28 @@ def latency(ev: np.ndarray, n_kernels: int = 4096, threshold: int | None = None)
         rec["sm"], rec["warp"] = e["sm_id"][i], e["warp_id"][i]
         out.append((int(i), rec.tobytes()))
     return hist, out
+
+
+def warp_heat(ev: np.ndarray, lanes: int = 32) -> Tuple[Dict[int, Tuple[int, int]], np.ndarray, np.ndarray]:
+    """({region: (count, last_ts)}, tally[16, 2], R0 per record) of the warp-level policy:
+    warps of `lanes` consecutive records (the last may be shorter); per warp lo / hi = the
+    lowest / highest addr >> 21, heat[lo] gains the lanes in region lo and the warp's ts,
+    tally[kind] one warp and the sizes, tally[9] the misaligned lanes; R0 = hi - lo."""
+    heat: Dict[int, Tuple[int, int]] = {}
+    tally = np.zeros((P.PAGE_HEAT_TALLY, 2), dtype=np.uint64)
+    r0 = np.zeros(len(ev), dtype=np.int64)
+    for w0 in range(0, len(ev), lanes):
+        w = ev[w0:w0 + lanes]
+        size, kind, ts = int(w["size"][0]), int(w["kind"][0]), int(w["ts_ns"][0])
+        if not (0 < size <= 4096 and size & (size - 1) == 0 and kind < 8):
+            tally[8, 0] += np.uint64(1)
+            continue
+        region = w["addr"] >> np.uint64(21)
+        lo, hi = int(region.min()), int(region.max())
+        count, last = heat.get(lo, (0, 0))
+        heat[lo] = (count + int(np.count_nonzero(region == lo)), max(last, ts))
+        tally[kind, 0] += np.uint64(1)
+        tally[kind, 1] += np.uint64(size * len(w))
+        tally[9, 0] += np.uint64(np.count_nonzero(w["addr"] & np.uint64(size - 1)))
+        r0[w0:w0 + lanes] = hi - lo
+    return heat, tally, r0

@@ -142,3 +142,32 @@ def test_random_program_lengths():
     progs = P.batch_programs()
     lens = [len(p[0]) for p in progs]
     assert len(progs) == 64 and min(lens) >= 10 and max(lens) <= 400
+
+
+def warp_heat_events(n_warps, seed, tail=13):
+    """Warp-context records with planted bad warps (size 3, kind 9), misaligned lanes and a
+    ragged last warp of `tail` lanes."""
+    ev = gen.warp_access_events(n_warps, seed=seed)
+    w = ev.reshape(n_warps, 32)
+    w["size"][::37] = 3
+    w["kind"][5::41] = 9
+    w["addr"][3::7, 4::9] |= np.uint64(1)
+    extra = gen.warp_access_events(1, seed=seed + 1)[:tail]
+    return np.concatenate([ev, extra])
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_warp_heat_is_a_per_warp_groupby(seed):
+    """The oracle's warp run of the warp-level policy equals its closed form: per warp the
+    lowest / highest region, the lanes in the lowest, the sizes and the misaligned lanes."""
+    prog, specs, cs = P.warp_heat()
+    ev = warp_heat_events(1500, seed)
+    maps = O.maps_from_specs(specs)
+    r0, _ = O.run_warps(prog, maps, ev, cs, uniform=gen.WARP_UNIFORM, want_r0=True)
+    heat, tally, want_r0 = CF.warp_heat(ev)
+    got = {int.from_bytes(k, "little"): (int.from_bytes(v[:8], "little"), int.from_bytes(v[8:], "little"))
+           for k, v in maps[0].hash_items().items()}
+    assert got == heat
+    assert np.array_equal(maps[1].array_u64(), tally)
+    assert np.array_equal(r0, want_r0)
+    assert tally[8, 0] > 0 and tally[9, 0] > 0 and (want_r0 > 0).any() and (want_r0 == 0).any()

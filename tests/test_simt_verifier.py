@@ -305,3 +305,28 @@ def test_accepted_handlers_never_diverge():
                 n_witness += 1
     assert n_acc >= 80 and n_rej >= 80, (n_acc, n_rej)
     assert n_witness >= 0.6 * n_rej, (n_witness, n_rej)
+
+
+def test_warp_heat_budgets_and_their_worst_path():
+    """The warp-level policy is a uniform handler over warp-context records.  Its worst path
+    (a valid warp that inserts its region and has misaligned lanes) runs 82 instructions,
+    12 helper calls and 19 memory operations, counted by hand along the program; the oracle
+    reaches exactly 82 on such a warp."""
+    prog, specs, cs = P.warp_heat()
+    rc, rep, log = gx.verify_simt(prog, specs, cs, gen.WARP_UNIFORM)
+    assert rc == 0, log
+    assert (rep.max_insns, rep.max_helper_calls, rep.max_mem_ops) == (82, 12, 19)
+    assert gx.verify_simt(prog, specs, cs, gen.WARP_UNIFORM, max_insns=81)[1].violation == gx.SIMT_V_INSNS
+    assert gx.verify_simt(prog, specs, cs, gen.WARP_UNIFORM, max_insns=82, max_helper_calls=12, max_mem_ops=19)[0] == 0
+    # the per-lane engine refuses its warp helpers; with the address also declared uniform
+    # nothing varies
+    assert gx.verify(prog, specs, cs)[0] == gx.E_VERIFY
+    assert gx.verify_simt(prog, specs, cs, np.ones(cs, bool))[1].varying_insns == 0
+    ev = gen.warp_access_events(200, seed=4)
+    ev["addr"][::3] |= np.uint64(1)  # misaligned lanes in every warp
+    raw = np.ascontiguousarray(ev).view(np.uint8).reshape(-1, cs)
+    assert per_warp_max_insns(prog, specs, raw, cs, gen.WARP_UNIFORM) == 82
+    # with the address lane-varying and no reduction in between, its region would be a key
+    lines = ["ldx8 r7 r1 0", "rsh r7 21", "stx8 r10 -8 r7", "ld_map r1 0", "mov r2 r10", "add r2 -8",
+             "call map_lookup_elem", "mov r0 0", "exit"]
+    rejected(lines, specs, gx.SIMT_V_KEY, 7, uniform=gen.WARP_UNIFORM, ctx_size=32)

@@ -41,3 +41,26 @@ def test_latency_pairs_shape():
     t = P.lognormal_quantile_ns(np.log(20000.0), 1.0, 0.99)
     assert abs(t - 204810) < 5
     assert 0.009 < np.mean(lat > t) < 0.011
+
+
+def test_warp_access_events():
+    """Warp-context records: every lane of a warp shares the warp's instruction fields, about
+    the requested fraction of warps is coalesced (consecutive size-strided addresses), and
+    the output depends on neither the thread count nor anything but the seed."""
+    n = 20_000
+    ev = gen.warp_access_events(n, seed=9, coalesced=0.75)
+    assert np.array_equal(ev, gen.warp_access_events(n, seed=9, coalesced=0.75, nthreads=1))
+    assert np.array_equal(ev, gen.warp_access_events(n, seed=9, coalesced=0.75, nthreads=6))
+    w = ev.reshape(n, 32)
+    for f in ("sm_id", "warp_id", "ts_ns", "kind", "size"):
+        assert (w[f] == w[f][:, :1]).all(), f
+    raw = ev.view(np.uint8).reshape(-1, 32).reshape(n, 32, 32)
+    assert (raw[:, :, gen.WARP_UNIFORM] == raw[:, :1, gen.WARP_UNIFORM]).all()
+    step = np.diff(w["addr"].astype(np.int64), axis=1)
+    coalesced = (step == w["size"][:, 1:].astype(np.int64)).all(axis=1)
+    assert 0.73 < coalesced.mean() < 0.77
+    assert np.all(w["addr"] % w["size"].astype(np.uint64) == 0)
+    assert np.all(np.diff(w["ts_ns"][:, 0].astype(np.int64)) >= 1)
+    assert not gen.warp_access_events(100, seed=9, coalesced=0.0).reshape(100, 32)["addr"].tolist() == \
+        gen.warp_access_events(100, seed=9, coalesced=1.0).reshape(100, 32)["addr"].tolist()
+    assert len(gen.warp_access_events(7, lanes=5)) == 35

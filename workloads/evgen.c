@@ -106,14 +106,15 @@ static uint64_t zipf_rank(const zipf_t *z, uint64_t seed, uint64_t i) {
 }
 
 /* ---------------- generation jobs ---------------- */
-enum { KIND_UNIFORM = 0, KIND_PAGEHEAT = 1, KIND_PAIRS = 2 };
+enum { KIND_UNIFORM = 0, KIND_PAGEHEAT = 1, KIND_PAIRS = 2, KIND_WARPS = 3 };
 
 typedef struct {
     int kind;
     uint64_t seed, n; /* n = records (uniform/pageheat) or pairs */
     ev_rec *out;
-    double p0, p1; /* pageheat: zipf s ; pairs: mu, sigma */
-    uint32_t u0;   /* pageheat: log2 pages ; pairs: kernel ids */
+    double p0, p1; /* pageheat: zipf s ; pairs: mu, sigma ; warps: zipf s, coalesced fraction */
+    uint32_t u0;   /* pageheat, warps: log2 pages ; pairs: kernel ids */
+    uint32_t u1;   /* warps: lanes per warp */
     zipf_t zipf;
     uint64_t *chunk_sum; /* per-chunk timestamp totals */
     int nthreads;
@@ -157,6 +158,33 @@ static void fill_item(const job_t *j, uint64_t i, uint64_t ts) {
         r->ts_ns = ts;
         r->kind = below(d3, 8);
         r->size = size;
+    } else if (j->kind == KIND_WARPS) { /* one warp: shared instruction fields, per-lane addresses */
+        uint64_t pages_mask = (1ULL << j->u0) - 1ULL;
+        uint32_t size = SIZE_CHOICES[below(d4, 4)];
+        int coalesced = unit(draw(j->seed, i, 5)) < j->p1;
+        uint64_t lane_seed = mix64(j->seed ^ 0xC0A1E5CEDULL); /* lanes draw from their own stream */
+        uint64_t base = 0;
+        if (coalesced) {
+            uint64_t rank = zipf_rank(&j->zipf, j->seed, i);
+            uint64_t page = ((rank - 1ULL) * 0x9E3779B1ULL + (j->seed & pages_mask)) & pages_mask;
+            base = (page << 12) | ((d1 & 4095ULL) & ~(uint64_t)(size - 1));
+        }
+        for (uint32_t l = 0; l < j->u1; l++) {
+            ev_rec *r = &j->out[i * j->u1 + l];
+            if (coalesced) {
+                r->addr = base + (uint64_t)l * size;
+            } else {
+                uint64_t li = i * j->u1 + l;
+                uint64_t rank = zipf_rank(&j->zipf, lane_seed, li);
+                uint64_t page = ((rank - 1ULL) * 0x9E3779B1ULL + (j->seed & pages_mask)) & pages_mask;
+                r->addr = (page << 12) | ((draw(lane_seed, li, 1) & 4095ULL) & ~(uint64_t)(size - 1));
+            }
+            r->sm_id = below(d2, 148);
+            r->warp_id = below(d2 << 32 | d2 >> 32, 64);
+            r->ts_ns = ts;
+            r->kind = below(d3, 8);
+            r->size = size;
+        }
     } else { /* entry/exit pair of one thread block */
         ev_rec *e = &j->out[2 * i], *x = &j->out[2 * i + 1];
         uint32_t kid = below(d1, j->u0);
@@ -251,6 +279,32 @@ int evgen_pageheat(uint64_t seed, uint64_t n, double s, uint32_t log2_pages, voi
     j.n = n;
     j.out = (ev_rec *)out;
     j.u0 = log2_pages;
+    zipf_init(&j.zipf, s, (double)(1ULL << log2_pages));
+    j.nthreads = nthreads;
+    return run_job(&j);
+}
+
+/*
+ * Warp-context memory-access records: n_warps * lanes records, warp w in records
+ * [w*lanes, (w+1)*lanes).  The lanes of a warp share sm_id, warp_id, ts_ns, kind and size
+ * (one instruction of one warp); a fraction `coalesced` of the warps touch consecutive
+ * size-strided addresses from one Zipf(s) page, the others one Zipf(s) page per lane.
+ */
+int evgen_warp_access(uint64_t seed, uint64_t n_warps, uint32_t lanes, double s, uint32_t log2_pages,
+                      double coalesced, void *out, int nthreads) {
+    if (lanes < 1 || lanes > 32 || log2_pages < 1 || log2_pages > 40 || !(s > 0.0) || s == 1.0 ||
+        !(coalesced >= 0.0 && coalesced <= 1.0))
+        return -22;
+    job_t j;
+    memset(&j, 0, sizeof j);
+    j.kind = KIND_WARPS;
+    j.seed = seed;
+    j.n = n_warps;
+    j.out = (ev_rec *)out;
+    j.u0 = log2_pages;
+    j.u1 = lanes;
+    j.p0 = s;
+    j.p1 = coalesced;
     zipf_init(&j.zipf, s, (double)(1ULL << log2_pages));
     j.nthreads = nthreads;
     return run_job(&j);

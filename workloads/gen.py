@@ -47,9 +47,10 @@ def lib() -> ctypes.CDLL:
             L.evgen_uniform.argtypes = [u64, u64, vp, i32]
             L.evgen_pageheat.argtypes = [u64, u64, dbl, u32, vp, i32]
             L.evgen_latency_pairs.argtypes = [u64, u64, dbl, dbl, u32, vp, i32]
+            L.evgen_warp_access.argtypes = [u64, u64, u32, dbl, u32, dbl, vp, i32]
             L.evgen_draw.argtypes = [u64, u64, u32]
             L.evgen_draw.restype = u64
-            for f in (L.evgen_uniform, L.evgen_pageheat, L.evgen_latency_pairs):
+            for f in (L.evgen_uniform, L.evgen_pageheat, L.evgen_latency_pairs, L.evgen_warp_access):
                 f.restype = i32
             _lib = L
     return _lib
@@ -83,6 +84,22 @@ def pageheat_events(n: int, seed: int = BASE_SEED, s: float = 1.1, log2_pages: i
     rc = lib().evgen_pageheat(seed, n, s, log2_pages, ev.ctypes.data, _threads(nthreads))
     assert rc == 0, rc
     return ev
+
+
+def warp_access_events(n_warps: int, seed: int = BASE_SEED, lanes: int = 32, s: float = 1.1, log2_pages: int = 24,
+                       coalesced: float = 0.75, out=None, nthreads=None) -> np.ndarray:
+    """n_warps * lanes records, one warp-context memory access per warp: the lanes of warp w
+    (records w*lanes ..) share sm_id, warp_id, ts_ns, kind and size; a fraction `coalesced`
+    of the warps access consecutive size-strided addresses from one Zipf(s) page, the
+    others one Zipf(s) page per lane."""
+    ev = _alloc(n_warps * lanes, out)
+    rc = lib().evgen_warp_access(seed, n_warps, lanes, s, log2_pages, coalesced, ev.ctypes.data, _threads(nthreads))
+    assert rc == 0, rc
+    return ev
+
+
+# the bytes of a warp-context record every lane of a warp shares (sm_id .. size); addr is per lane
+WARP_UNIFORM = np.array([False] * 8 + [True] * 24)
 
 
 def latency_pairs(n_pairs: int, seed: int = BASE_SEED, mu: float = float(np.log(20000.0)), sigma: float = 1.0,

@@ -11,6 +11,9 @@ tests and the engine tests; they carry no execution semantics.
                 an 8-iteration bounded loop and a per-kind tally.
 * latency    -- a `kernelretsnoop`-style tool (Sec. 6.4): block exit - entry latency,
                 log2 histogram per kernel id, outliers emitted to a ring buffer.
+* warp_heat  -- page_heat's policy as a warp-level handler (Sec. 4.4.1-4.4.2) over
+                warp-context records: lane addresses reach the maps only through warp
+                reductions; for SIMT-aware verification and the oracle's warp run.
 * random_program -- seed-generated verifier-friendly programs for the multi-program batch.
 """
 from __future__ import annotations
@@ -173,6 +176,128 @@ def page_heat(max_entries: int = 1 << 20) -> Tuple[np.ndarray, List[MapSpec], in
     a.ld_map("r1", 1)
     a.mov("r2", "r10")
     a.add("r2", -28)
+    a.call("map_lookup_elem")
+    a.jeq("r0", 0, "bad_out")
+    a.mov("r1", 1)
+    a.atomic(8, "add", "r0", 0, "r1")
+    a.label("bad_out")
+    a.mov("r0", 0)
+    a.exit()
+    return a.prog(), [hash_spec(max_entries, 8, 16, insert_only=True), array_spec(PAGE_HEAT_TALLY, 16)], 32
+
+
+def warp_heat(max_entries: int = 1 << 16) -> Tuple[np.ndarray, List[MapSpec], int]:
+    """A warp-level memory-access policy (Sec. 4.4.1, Sec. 4.4.2) over warp-context records
+    (`gen.warp_access_events`): one handler per warp, lanes in lockstep, side effects once.
+
+    size and kind are warp-uniform and validated as in `page_heat` (a bad warp counts once in
+    tally[8] and returns 0).  Lane-varying addresses reach shared state only through warp
+    reductions: lo / hi = the lowest / highest 2 MiB region any lane touches, n_in = the lanes
+    in region lo, n_mis = the lanes whose address is not size-aligned.  Then heat[lo] =
+    {count += n_in, last_ts = max(ts)}, tally[kind] = {warps += 1, bytes += sum of sizes},
+    tally[9] += n_mis, and R0 = hi - lo (the warp's region spread) in every lane.
+    Maps: 0 = hash(u64 -> {u64 count, u64 last_ts}), 1 = array[16] of {u64, u64}.
+    Accepted by SIMT-aware verification with the warp-uniform bytes `gen.WARP_UNIFORM`; the
+    per-lane engine refuses its warp helpers.
+    """
+    a = Asm()
+    a.mov("r6", "r1")
+    a.ldx(8, "r7", "r6", F_ADDR)
+    a.ldx(8, "r8", "r6", F_TS)
+    a.ldx(4, "r2", "r6", F_SIZE)
+    a.ldx(4, "r3", "r6", F_KIND)
+    a.jeq("r2", 0, "bad")
+    a.jgt("r2", 4096, "bad")
+    a.mov("r4", "r2")
+    a.add("r4", -1)
+    a.alu("and", "r4", "r2")
+    a.jne("r4", 0, "bad")
+    a.jgt("r3", 7, "bad")
+    # n_mis: lanes whose address is not size-aligned
+    a.mov("r1", "r2")
+    a.add("r1", -1)
+    a.alu("and", "r1", "r7")
+    a.call("warp_count")
+    a.mov("r9", "r0")
+    # lo, hi: the warp's lowest and highest 2 MiB region
+    a.rsh("r7", 21)
+    a.mov("r1", "r7")
+    a.call("warp_min_u64")
+    a.stx(8, "r10", -8, "r0")
+    a.mov("r1", "r7")
+    a.call("warp_max_u64")
+    a.stx(8, "r10", -32, "r0")
+    # n_in = lanes - lanes outside region lo
+    a.mov("r1", "r7")
+    a.ldx(8, "r2", "r10", -8)
+    a.alu("sub", "r1", "r2")
+    a.call("warp_count")
+    a.mov("r7", "r0")
+    a.mov("r1", 1)
+    a.call("warp_count")
+    a.alu("sub", "r0", "r7")
+    a.mov("r7", "r0")
+    # heat[lo]: the insert idiom, then the updates
+    a.ld_map("r1", 0)
+    a.mov("r2", "r10")
+    a.add("r2", -8)
+    a.call("map_lookup_elem")
+    a.jne("r0", 0, "have")
+    a.st(8, "r10", -24, 0)
+    a.st(8, "r10", -16, 0)
+    a.ld_map("r1", 0)
+    a.mov("r2", "r10")
+    a.add("r2", -8)
+    a.mov("r3", "r10")
+    a.add("r3", -24)
+    a.mov("r4", BPF_NOEXIST)
+    a.call("map_update_elem")
+    a.ld_map("r1", 0)
+    a.mov("r2", "r10")
+    a.add("r2", -8)
+    a.call("map_lookup_elem")
+    a.jeq("r0", 0, "tally")
+    a.label("have")
+    a.atomic(8, "add", "r0", 0, "r7")
+    a.mov("r1", "r0")
+    a.add("r1", 8)
+    a.mov("r2", "r8")
+    a.call("atomic_max_u64")
+    # tally[kind] += {1, sum of sizes}
+    a.label("tally")
+    a.ldx(4, "r1", "r6", F_SIZE)
+    a.call("warp_sum_u64")
+    a.mov("r7", "r0")
+    a.ldx(4, "r3", "r6", F_KIND)
+    a.stx(4, "r10", -36, "r3")
+    a.ld_map("r1", 1)
+    a.mov("r2", "r10")
+    a.add("r2", -36)
+    a.call("map_lookup_elem")
+    a.jeq("r0", 0, "mis")
+    a.mov("r1", 1)
+    a.atomic(8, "add", "r0", 0, "r1")
+    a.atomic(8, "add", "r0", 8, "r7")
+    # tally[9] += n_mis
+    a.label("mis")
+    a.jeq("r9", 0, "out")
+    a.st(4, "r10", -36, 9)
+    a.ld_map("r1", 1)
+    a.mov("r2", "r10")
+    a.add("r2", -36)
+    a.call("map_lookup_elem")
+    a.jeq("r0", 0, "out")
+    a.atomic(8, "add", "r0", 0, "r9")
+    a.label("out")
+    a.ldx(8, "r0", "r10", -32)
+    a.ldx(8, "r1", "r10", -8)
+    a.alu("sub", "r0", "r1")
+    a.exit()
+    a.label("bad")
+    a.st(4, "r10", -36, 8)
+    a.ld_map("r1", 1)
+    a.mov("r2", "r10")
+    a.add("r2", -36)
     a.call("map_lookup_elem")
     a.jeq("r0", 0, "bad_out")
     a.mov("r1", 1)
