@@ -316,6 +316,17 @@ typedef struct gx_simt_report {
 int gx_verify_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, const gx_simt_spec *simt, gx_simt_report *out, char *log,
                    size_t log_len);
+/*
+ * Host only: SIMT-verify a program (as gx_verify_simt) and compile its warp-level form for
+ * sm_103a without loading it (NVRTC must be available; no device needed).  In that form the
+ * 32 lanes of a warp run the handler over 32 consecutive events; helper calls, and stores
+ * and atomics outside the lane's stack, run on the warp's first valid lane with their
+ * results broadcast; the warp helpers reduce over the valid lanes.  No entry point loads
+ * this form yet.  0, GX_E_VERIFY, GX_E_NODEV (no runtime compiler) or GX_E_CUDA (compile
+ * error); `log` explains.
+ */
+int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+                      const gx_prog_opts *opts, const gx_simt_spec *simt, char *log, size_t log_len);
 
 /* Verify, decode and upload a program; it holds a reference on each map. */
 int gx_verify_load(gx_ctx *ctx, const uint64_t *insns, uint32_t n_insns, gx_map *const *maps, uint32_t n_maps,

@@ -8,5 +8,5 @@ from .gx import (  # noqa: F401
     ENOENT, ENOMEM, EXIST, MAP_ARRAY, MAP_F_NO_DELETE, MAP_HASH, MAP_RINGBUF, NOEXIST, SHARDS_AGG, SHARDS_OFF, Batch, Context, GxError, Map, Program,
     Server, VARIANT_CAPPED, VARIANT_WIDE, analyze, check, exported_symbols, jit_check, lib, now, parse_records, verify,
     SIMT_V_ATOMIC, SIMT_V_BRANCH, SIMT_V_HELPER, SIMT_V_HELPERS, SIMT_V_INSNS, SIMT_V_KEY, SIMT_V_MEM, SIMT_V_NONE,
-    SIMT_V_RET, SIMT_V_STORE, SIMT_V_VERIFY, SimtReport, verify_simt,
+    SIMT_V_RET, SIMT_V_STORE, SIMT_V_VERIFY, SimtReport, jit_check_simt, verify_simt,
 )

@@ -487,13 +487,7 @@ int gx_verify_simt(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, u
     }
     if (!insns || !opts || !simt || (n_maps && !maps) || simt->reserved) return GX_EINVAL;
     if (opts->ctx_size < 8 || opts->ctx_size > GX_MAX_CTX) return GX_EINVAL;
-    SimtIn in;
-    in.uniform.assign(opts->ctx_size, 0);
-    if (simt->uniform)
-        for (uint32_t b = 0; b < opts->ctx_size; b++) in.uniform[b] = simt->uniform[b] != 0;
-    in.max_insns = simt->max_insns;
-    in.max_helpers = simt->max_helper_calls;
-    in.max_mem = simt->max_mem_ops;
+    const SimtIn in = simt_in(*simt, opts->ctx_size);
     VerifyOut v;
     int rc = verify_program(insns, n, maps, n_maps, *opts, v, &in);
     if (rc == GX_E_VERIFY && v.simt.violation == GX_SIMT_V_NONE) {

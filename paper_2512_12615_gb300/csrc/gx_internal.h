@@ -54,6 +54,16 @@ struct SimtIn {
     std::vector<uint8_t> uniform; /* per ctx byte: nonzero = warp-uniform */
     uint32_t max_insns = 0, max_helpers = 0, max_mem = 0; /* per-path budgets, 0 = unlimited */
 };
+inline SimtIn simt_in(const gx_simt_spec &spec, uint32_t ctx_size) {
+    SimtIn in;
+    in.uniform.assign(ctx_size, 0);
+    if (spec.uniform)
+        for (uint32_t b = 0; b < ctx_size; b++) in.uniform[b] = spec.uniform[b] != 0;
+    in.max_insns = spec.max_insns;
+    in.max_helpers = spec.max_helper_calls;
+    in.max_mem = spec.max_mem_ops;
+    return in;
+}
 struct SimtOut {
     uint64_t max_insns = 0;
     uint32_t max_helpers = 0, max_mem = 0;

@@ -20,6 +20,7 @@ struct JitProgram {
     std::vector<MapUse> use;       /* per map: may its updates be combined per block? */
     uint32_t ctx_size = 8;         /* bytes per event record */
     uint64_t budget = 1ull << 16;
+    bool warp = false; /* a SIMT-verified warp-level handler: shared effects once per warp, by its leader lane */
 };
 
 struct JitKernel {

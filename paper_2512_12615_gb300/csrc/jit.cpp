@@ -10,7 +10,8 @@
  * runtime's library API.  A kernel may hold several programs (a batch): it switches on
  * the chunk's program slot.  NVRTC is loaded with dlopen, so the engine library keeps
  * loading on hosts without the compiler or a GPU; compiled cubins are cached in memory
- * and, if GX_JIT_CACHE names a directory, on disk.
+ * and, if GX_JIT_CACHE names a directory, on disk.  If GX_JIT_DUMP_DIR names a directory,
+ * every generated source is also written there as <key>.cu, for reading.
  */
 #include <cuda_runtime.h>
 #include <dlfcn.h>
@@ -376,9 +377,16 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         if (p.info[pc].visited && p.info[pc].stk_any && p.info[pc].kind != MK_STACK) scalar = false;
     std::ostringstream o;
     o << "__device__ __forceinline__ u64 gx_body_" << slot
-      << "(const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {\n"
-      << "  if (!valid) return 0;\n"
+      << "(const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {\n";
+    /*
+     * Warp-level handler (SIMT-verified): the 32 lanes hold 32 consecutive events and follow
+     * one path; helper calls and stores / atomics outside the lane's stack run on the first
+     * valid lane and their results are broadcast; warp helpers reduce over the valid lanes.
+     */
+    if (p.warp) o << "  const u32 wmask = __ballot_sync(0xFFFFFFFFu, valid);\n";
+    o << "  if (!valid) return 0;\n"
       << "  const u32 lane = threadIdx.x & 31;\n";
+    if (p.warp) o << "  const u32 leader = (u32)__ffs(wmask) - 1u;\n  const bool lead = lane == leader;\n";
     if (scalar) {
         o << "  u64 stk_mem[" << GX_STACK_BYTES / 8 << "];\n  u64 ";
         for (int k = 0; k < GX_STACK_BYTES / 8; k++) o << (k ? ", s" : "s") << k << " = 0";
@@ -471,6 +479,12 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                 o << "return r0;";
                 break;
             }
+            if (code == 0x80 && p.warp && imm >= GX_HELPER_WARP_SUM_U64 && imm <= GX_HELPER_WARP_COUNT) {
+                static const char *red[] = {"AG_ADD", "AG_MAX", "AG_MIN", "AG_OR", "AG_AND"};
+                if (imm == GX_HELPER_WARP_COUNT) o << "r0 = (u64)__popc(__ballot_sync(wmask, r1 != 0ull));";
+                else o << "r0 = group_reduce<" << red[imm - GX_HELPER_WARP_SUM_U64] << ", 8>(wmask, r1);";
+                break;
+            }
             if (code == 0x80) {
                 std::string m = ii.map >= 0 ? "env.maps[" + std::to_string(ii.map) + "]" : "env.maps[r1]";
                 const bool inline_lookup = imm == GX_HELPER_MAP_LOOKUP && ii.map >= 0 && ii.map < (int)p.maps.size() &&
@@ -483,6 +497,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     imm != GX_HELPER_RINGBUF_SUBMIT && imm != GX_HELPER_RINGBUF_DISCARD &&
                     imm != GX_HELPER_RINGBUF_RESERVE)
                     o << mat(ii, imm == GX_HELPER_MAP_UPDATE);
+                if (p.warp) o << "if (lead) { ";
                 switch (imm) {
                 case GX_HELPER_MAP_LOOKUP: {
                     /* one map and a key at a known stack slot: inline, per lane, layout as constants */
@@ -535,6 +550,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     break;
                 default: log = "jit: unknown helper"; return GX_EINVAL;
                 }
+                if (p.warp) o << " } r0 = __shfl_sync(wmask, r0, leader);";
                 break;
             }
             const char *c = cond_op(code);
@@ -597,6 +613,20 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             std::string addr = ii.kind == MK_STACK
                                    ? "(u64)((uint8_t *)stack + " + std::to_string(ii.off + GX_STACK_BYTES) + ")"
                                    : "(" + R(dst) + " + " + hex64((uint64_t)(int64_t)off) + ")";
+            /* warp-level handler: outside the lane's stack the leader writes, the fetched value is broadcast */
+            std::string bcast;
+            if (p.warp && ii.kind != MK_STACK) {
+                o << "{ const u64 wa_ = " << addr << "; const bool sh_ = !__isLocal((const void *)wa_); if (!sh_ || lead) { ";
+                addr = "wa_"; /* gen_update declares its own a_ */
+                if ((op & 0xE0) == 0xC0 && imm == 0xF1) bcast = "r0";
+                else if ((op & 0xE0) == 0xC0 && (imm & 1)) bcast = R(src);
+            }
+            auto close = [&]() {
+                if (!p.warp || ii.kind == MK_STACK) return;
+                o << " }";
+                if (!bcast.empty()) o << " if (sh_) " << bcast << " = __shfl_sync(wmask, " << bcast << ", leader);";
+                o << " }";
+            };
             if ((op & 0xE0) == 0xC0) {
                 std::string sz = std::to_string(size);
                 if (imm == 0xE1) o << R(src) << " = xchg<" << sz << ">(" << addr << ", " << R(src) << ");";
@@ -608,17 +638,20 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     else if (ii.kind == MK_STACK) o << "agg_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ", __activemask());";
                     else o << gen_update(sp, ii, ag, size, addr, R(src));
                 }
+                close();
                 break;
             }
             std::string v = cls == 3 ? R(src) : hex64((uint64_t)(int64_t)imm);
             o << "store_sz<" << size << ">((uint8_t *)" << addr << ", " << v << ");";
+            close();
             break;
         }
         }
         o << "\n";
     }
     o << "budget_trip:\n"
-      << "  atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);\n"
+      << (p.warp ? "  if (lead) atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);\n" /* one handler per warp */
+                 : "  atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);\n")
       << "  set_status(env.stats, GX_E_BUDGET);\n"
       << "  return 0;\n}\n\n";
     out += o.str();
@@ -735,6 +768,11 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
 
 /* generated source -> cubin (disk cache first, then NVRTC) */
 int jit_cubin(const std::string &src, const std::string &key, std::vector<char> &cubin, std::string &log) {
+    const char *dump = getenv("GX_JIT_DUMP_DIR");
+    if (dump && *dump) {
+        mkdir(dump, 0755);
+        write_file(std::string(dump) + "/" + key + ".cu", std::vector<char>(src.begin(), src.end()));
+    }
     const char *dir = getenv("GX_JIT_CACHE");
     std::string path = dir && *dir ? std::string(dir) + "/" + key + ".cubin" : "";
     if (!path.empty() && read_file(path, cubin)) return GX_OK;
@@ -858,6 +896,35 @@ extern "C" int gx_jit_check(const uint64_t *insns, uint32_t n, const gx_map_spec
         jp.use = v.map_use;
         jp.ctx_size = opts->ctx_size;
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        const std::string src = gx::jit_source({&jp}, msg, rc);
+        std::vector<char> cubin;
+        if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, msg.size());
+        memcpy(log, msg.data(), k);
+        log[k] = 0;
+    }
+    return rc;
+}
+
+extern "C" int gx_jit_check_simt(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                                 const gx_prog_opts *opts, const gx_simt_spec *simt, char *log, size_t log_len) {
+    if (!insns || !opts || !simt || (n_maps && !maps) || simt->reserved) return GX_EINVAL;
+    if (opts->ctx_size < 8 || opts->ctx_size > GX_MAX_CTX) return GX_EINVAL;
+    const gx::SimtIn in = gx::simt_in(*simt, opts->ctx_size);
+    gx::VerifyOut v;
+    int rc = gx::verify_program(insns, n, maps, n_maps, *opts, v, &in);
+    std::string msg = v.log;
+    if (rc == GX_OK) {
+        gx::JitProgram jp;
+        jp.insns.assign(insns, insns + n);
+        jp.info = v.info;
+        jp.maps.assign(maps, maps + n_maps);
+        jp.use = v.map_use;
+        jp.ctx_size = opts->ctx_size;
+        jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        jp.warp = true;
         const std::string src = gx::jit_source({&jp}, msg, rc);
         std::vector<char> cubin;
         if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);

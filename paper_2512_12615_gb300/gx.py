@@ -123,6 +123,8 @@ _SIGS = {
                            ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_simt": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                              ctypes.POINTER(SimtSpec), ctypes.POINTER(SimtReport), ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_jit_check_simt": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                                ctypes.POINTER(SimtSpec), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
                              ctypes.POINTER(ProgOpts), ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                              ctypes.c_size_t]),
@@ -240,17 +242,37 @@ def verify_simt(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, uni
     insns = np.ascontiguousarray(insns, dtype=np.uint64)
     specs = _specs(map_specs)
     opts = ProgOpts(ctx_size, int(deterministic), insn_budget, 0, 0)
+    spec, keep = _simt_spec(ctx_size, uniform, max_insns, max_helper_calls, max_mem_ops)
+    out = SimtReport()
+    log = ctypes.create_string_buffer(1024)
+    rc = lib().gx_verify_simt(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
+                              ctypes.byref(spec), ctypes.byref(out), log, 1024)
+    del keep
+    return rc, out, log.value.decode()
+
+
+def _simt_spec(ctx_size: int, uniform, max_insns: int, max_helper_calls: int, max_mem_ops: int):
     uni = None
     if uniform is not None:
         uni = np.ascontiguousarray(np.asarray(uniform, dtype=bool).astype(np.uint8))
         if uni.size != ctx_size:
             raise ValueError(f"uniform has {uni.size} flags for a {ctx_size}-byte ctx")
-    spec = SimtSpec(None if uni is None else uni.ctypes.data, max_insns, max_helper_calls, max_mem_ops, 0)
-    out = SimtReport()
-    log = ctypes.create_string_buffer(1024)
-    rc = lib().gx_verify_simt(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
-                              ctypes.byref(spec), ctypes.byref(out), log, 1024)
-    return rc, out, log.value.decode()
+    return SimtSpec(None if uni is None else uni.ctypes.data, max_insns, max_helper_calls, max_mem_ops, 0), uni
+
+
+def jit_check_simt(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, uniform=None, *,
+                   max_insns: int = 0, max_helper_calls: int = 0, max_mem_ops: int = 0,
+                   insn_budget: int = 0) -> Tuple[int, str]:
+    """Host-only: SIMT-verify and compile the warp-level form (gx_jit_check_simt): (status, log)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    specs = _specs(map_specs)
+    opts = ProgOpts(ctx_size, 0, insn_budget, 0, 0)
+    spec, keep = _simt_spec(ctx_size, uniform, max_insns, max_helper_calls, max_mem_ops)
+    log = ctypes.create_string_buffer(1 << 20)
+    rc = lib().gx_jit_check_simt(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
+                                 ctypes.byref(spec), log, 1 << 20)
+    del keep
+    return rc, log.value.decode()
 
 
 PROG_JIT = 1

@@ -81,3 +81,159 @@ def test_ring_output_from_scalar_stack_compiles():
     lines = ["ldx8 r2 r1 0", "stx8 r10 -16 r2", "st8 r10 -8 5", "ld_map r1 0", "mov r2 r10", "add r2 -16",
              "mov r3 16", "mov r4 0", "call ringbuf_output", "mov r0 0", "exit"]
     _check(assemble(lines).prog(), [dict(type=27, key_size=0, value_size=0, max_entries=4096)], 16, det=False)
+
+
+# ---------------------------------------------------------------- warp-level form (compile only)
+# ctx 32 bytes: word 0 lane-varying, words 1..3 warp-uniform
+WARP_UNI = [False] * 8 + [True] * 24
+EVERY_EFFECT = """
+mov r9 r1
+ldx8 r6 r9 0
+ldx8 r7 r9 8
+mov r1 r6
+call warp_sum_u64
+mov r8 r0
+mov r1 r6
+call warp_or_u64
+add r8 r0
+mov r1 r6
+call warp_and_u64
+add r8 r0
+mov r1 r6
+call warp_max_u64
+add r8 r0
+mov r1 r6
+call warp_min_u64
+add r8 r0
+mov r1 r6
+call warp_count
+add r8 r0
+st8 r10 -8 0
+atomic8 add r10 -8 r6
+mov r2 r10
+add r2 -16
+jeq r7 0 slot
+mov r2 r10
+add r2 -24
+slot:
+st8 r2 0 5
+mov r1 r7
+and r1 3
+stx4 r10 -28 r1
+ld_map r1 0
+mov r2 r10
+add r2 -28
+call map_lookup_elem
+jeq r0 0 skip
+mov r5 r0
+mov r1 r8
+atomic8 add_fetch r5 0 r1
+mov r1 7
+atomic8 xchg r5 8 r1
+mov r0 0
+mov r1 9
+atomic8 cmpxchg r5 16 r1
+stx8 r5 24 r8
+mov r1 r5
+mov r2 r8
+call atomic_min_u64
+skip:
+stx8 r10 -40 r7
+stx8 r10 -48 r8
+ld_map r1 1
+mov r2 r10
+add r2 -40
+mov r3 r10
+add r3 -48
+mov r4 0
+call map_update_elem
+ld_map r1 1
+mov r2 r10
+add r2 -40
+call map_delete_elem
+ld_map r1 2
+mov r2 16
+mov r3 0
+call ringbuf_reserve
+jeq r0 0 one
+stx8 r0 0 r8
+st8 r0 8 1
+mov r1 r0
+mov r2 0
+call ringbuf_submit
+one:
+ld_map r1 2
+mov r2 8
+mov r3 0
+call ringbuf_reserve
+jeq r0 0 two
+mov r1 r0
+mov r2 0
+call ringbuf_discard
+two:
+stx8 r10 -56 r8
+ld_map r1 2
+mov r2 r10
+add r2 -56
+mov r3 8
+mov r4 0
+call ringbuf_output
+mov r0 r8
+exit
+""".strip().splitlines()
+EVERY_EFFECT_SPECS = [dict(type=2, key_size=4, value_size=32, max_entries=4),
+                      dict(type=1, key_size=8, value_size=8, max_entries=64),
+                      dict(type=27, key_size=0, value_size=0, max_entries=1 << 16)]
+
+
+def _check_warp(prog, specs, cs, uniform):
+    rc, log = gx.jit_check_simt(prog, specs, cs, uniform)
+    if rc == gx.E_NODEV:
+        pytest.skip("no runtime compiler on this host")
+    assert rc == 0, log
+
+
+def test_warp_form_of_every_shared_effect_compiles():
+    """Helpers, fetches, exchanges, stores and ring-buffer records on the leader lane with
+    their results broadcast; warp helpers; lane-private stack atomics; stack slots at
+    path-dependent offsets (the addressable stack)."""
+    import numpy as np
+
+    import oracle as O
+    from tests.test_simt_verifier import random_warps
+
+    prog = assemble(EVERY_EFFECT).prog()
+    rc, rep, log = gx.verify_simt(prog, EVERY_EFFECT_SPECS, 32, WARP_UNI)
+    assert rc == 0 and rep.varying_insns > 0, log
+    # the oracle's warp run takes it without a disagreement
+    ev = random_warps(np.random.default_rng(3), [False, True, True, True])
+    O.run_warps(prog, O.maps_from_specs(EVERY_EFFECT_SPECS), ev, 32, uniform=WARP_UNI)
+    _check_warp(prog, EVERY_EFFECT_SPECS, 32, WARP_UNI)
+
+
+def test_warp_form_of_warp_heat_compiles():
+    from workloads import gen
+
+    _check_warp(*P.warp_heat(), gen.WARP_UNIFORM)
+
+
+def test_warp_form_of_random_handlers_compiles():
+    import numpy as np
+
+    from tests.test_simt_verifier import RANDOM_SPECS, random_handler
+
+    rng = np.random.default_rng(77)
+    done = 0
+    while done < 3:
+        lines = random_handler(rng)
+        uniform = np.repeat(rng.random(4) < 0.5, 8)
+        prog = assemble(lines).prog()
+        if gx.verify_simt(prog, RANDOM_SPECS, 32, uniform)[0] != 0:
+            continue
+        _check_warp(prog, RANDOM_SPECS, 32, uniform)
+        done += 1
+
+
+def test_warp_form_needs_simt_verification():
+    rc, log = gx.jit_check_simt(assemble(["ldx8 r0 r1 0", "exit"]).prog(), [], 16, [False] * 16)
+    assert rc == gx.E_VERIFY and "lane-varying" in log
