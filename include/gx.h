@@ -328,6 +328,37 @@ int gx_verify_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *m
 int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
                       const gx_prog_opts *opts, const gx_simt_spec *simt, char *log, size_t log_len);
 
+/*
+ * Host only: how to merge copies of map `map_index` that several engines (one per GPU,
+ * each with its own maps) built by running this program over disjoint parts of one batch
+ * (Sec. 5.3: GPU-local map shards merged into a canonical snapshot).  The program is
+ * verified in deterministic mode whatever opts->deterministic says: that mode is what makes
+ * the merge exact.  word_ops (ceil(value_size / 4) entries) receives, per 4-byte word of a
+ * value, the update that changes it: GX_MERGE_NONE (never changed) or GX_MERGE_ADD / _OR /
+ * _AND / _XOR / _MAX / _MIN, with GX_MERGE_W8 set when the update is 64 bits wide (both
+ * words of the 8-byte pair carry it).  insert_value (value_size bytes, nullable) receives
+ * the constant bytes a hash insert writes and *has_insert (nullable) whether the program
+ * inserts into this map at all.  A word merges over the copies that hold the entry, with i
+ * its starting value (the array's contents before the runs; insert_value for a new hash
+ * key): ADD i + sum(v - i) and XOR i ^ xor(v ^ i), both modulo the width; OR, AND, MAX and
+ * MIN (unsigned) are the operation over the copies.  Hash maps merge as the union of their
+ * keys; ring buffers as the records of all copies ordered by event index (no ops needed).
+ * Returns 0, GX_E_VERIFY (rejected in deterministic mode) or GX_EINVAL (bad arguments, or
+ * copies that cannot be merged: a word updated at two widths, or inserts of different
+ * constants; `log` says which).
+ */
+#define GX_MERGE_NONE 0u
+#define GX_MERGE_ADD 1u
+#define GX_MERGE_OR 2u
+#define GX_MERGE_AND 3u
+#define GX_MERGE_XOR 4u
+#define GX_MERGE_MAX 5u
+#define GX_MERGE_MIN 6u
+#define GX_MERGE_W8 0x10u
+int gx_merge_ops(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+                 const gx_prog_opts *opts, uint32_t map_index, uint8_t *word_ops, uint8_t *insert_value,
+                 uint32_t *has_insert, char *log, size_t log_len);
+
 /* Verify, decode and upload a program; it holds a reference on each map. */
 int gx_verify_load(gx_ctx *ctx, const uint64_t *insns, uint32_t n_insns, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len);

@@ -9,4 +9,6 @@ from .gx import (  # noqa: F401
     Server, VARIANT_CAPPED, VARIANT_WIDE, analyze, check, exported_symbols, jit_check, lib, now, parse_records, verify,
     SIMT_V_ATOMIC, SIMT_V_BRANCH, SIMT_V_HELPER, SIMT_V_HELPERS, SIMT_V_INSNS, SIMT_V_KEY, SIMT_V_MEM, SIMT_V_NONE,
     SIMT_V_RET, SIMT_V_STORE, SIMT_V_VERIFY, SimtReport, jit_check_simt, verify_simt,
+    MERGE_ADD, MERGE_AND, MERGE_MAX, MERGE_MIN, MERGE_NONE, MERGE_OR, MERGE_W8, MERGE_XOR, merge_ops,
 )
+from . import merge  # noqa: F401,E402

@@ -479,6 +479,47 @@ int gx_analyze(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint3
     return rc;
 }
 
+int gx_merge_ops(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                 const gx_prog_opts *opts, uint32_t map_index, uint8_t *word_ops, uint8_t *insert_value,
+                 uint32_t *has_insert, char *log, size_t log_len) {
+    if (!insns || !opts || !word_ops || (n_maps && !maps) || map_index >= n_maps) return GX_EINVAL;
+    static_assert(UC_ADD == GX_MERGE_ADD && UC_OR == GX_MERGE_OR && UC_AND == GX_MERGE_AND && UC_XOR == GX_MERGE_XOR &&
+                      UC_MAX == GX_MERGE_MAX && UC_MIN == GX_MERGE_MIN && UC_W8 == GX_MERGE_W8,
+                  "the ABI's merge codes are the verifier's update classes");
+    gx_prog_opts det = *opts;
+    det.deterministic = 1;
+    VerifyOut v;
+    int rc = verify_program(insns, n, maps, n_maps, det, v);
+    std::string msg = v.log;
+    const uint32_t words = (maps[map_index].value_size + 3) / 4;
+    if (rc == GX_OK && maps[map_index].type != GX_MAP_RINGBUF) {
+        const MapUse &u = v.map_use[map_index];
+        if (u.merge_mixed) {
+            rc = GX_EINVAL;
+            msg = "map " + std::to_string(map_index) + ": a word is updated at two widths; its copies cannot be merged";
+        } else if (u.insert_conflict) {
+            rc = GX_EINVAL;
+            msg = "map " + std::to_string(map_index) + ": inserts of different constants; its copies cannot be merged";
+        } else {
+            memcpy(word_ops, u.merge_op.data(), words);
+            if (insert_value) {
+                memset(insert_value, 0, maps[map_index].value_size);
+                if (u.insert_seen) memcpy(insert_value, u.insert.data(), maps[map_index].value_size);
+            }
+            if (has_insert) *has_insert = u.insert_seen ? 1u : 0u;
+        }
+    } else if (rc == GX_OK) {
+        memset(word_ops, 0, words);
+        if (has_insert) *has_insert = 0;
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, msg.size());
+        memcpy(log, msg.data(), k);
+        log[k] = 0;
+    }
+    return rc;
+}
+
 int gx_verify_simt(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, const gx_simt_spec *simt, gx_simt_report *out, char *log, size_t log_len) {
     if (out) {

@@ -41,6 +41,16 @@ struct MapUse {
                                 or updated at a variable offset */
     bool mixed = false;      /* a word updated by two different operations or widths */
     std::vector<uint8_t> op; /* per 4-byte word of the value: UpdClass | UC_W8 for 8-byte operations */
+    /*
+     * Deterministic mode, for merging copies of the map built by several engines: per 4-byte
+     * word the class of every update (any offset, fetching or not; UpdClass | UC_W8), and the
+     * constant bytes the hash inserts write.  A word updated at two widths, or inserts of two
+     * different constants, make the copies unmergeable.
+     */
+    std::vector<uint8_t> merge_op;
+    bool merge_mixed = false;
+    std::vector<uint8_t> insert;
+    bool insert_seen = false, insert_conflict = false;
     bool combinable() const {
         if (other || mixed) return false;
         for (uint8_t c : op)

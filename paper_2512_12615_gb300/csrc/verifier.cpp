@@ -689,6 +689,15 @@ struct Verifier {
             if (r.cls != cls && lo < r.hi && r.lo < hi)
                 return fail(pc, "map memory updated by two different atomic operations (order-dependent)");
         op_ranges[p.map].push_back(OpRange{lo, hi, cls});
+        /* the words this update may change, for merging copies (8-byte updates are 8-aligned) */
+        static_assert(OPC_ADD == UC_ADD && OPC_MIN == UC_MIN, "one numbering for update classes");
+        MapUse &u = out->map_use[p.map];
+        const uint8_t code = (uint8_t)(cls | (size == 8 ? UC_W8 : 0));
+        const s64 a = std::max<s64>(lo, 0) & ~(s64)(size - 1), b = (hi + size - 1) & ~(s64)(size - 1);
+        for (s64 w = a / 4; w < (b + 3) / 4 && w < (s64)u.merge_op.size(); w++) {
+            if (u.merge_op[(size_t)w] == UC_NONE) u.merge_op[(size_t)w] = code;
+            else if (u.merge_op[(size_t)w] != code) u.merge_mixed = true;
+        }
         return GX_OK;
     }
 
@@ -1453,6 +1462,18 @@ struct Verifier {
                 if (!is_const(s.r[4]) || s.r[4].umin != GX_NOEXIST)
                     return fail(pc, "deterministic mode allows only NOEXIST inserts");
                 if (!vc) return fail(pc, "deterministic mode: inserted value must be constant bytes");
+                /* the constant bytes (whole constant spills) this insert writes, for merging copies */
+                MapUse &u = out->map_use[s.r[1].map];
+                std::vector<uint8_t> bytes(m.value_size);
+                const int b0 = (int)s.r[3].smin + GX_STACK_BYTES;
+                for (u32 k = 0; k < m.value_size; k++)
+                    bytes[k] = (uint8_t)(s.spill[(b0 + (int)k) / 8].umin >> (8 * ((b0 + (int)k) % 8)));
+                if (!u.insert_seen) {
+                    u.insert = bytes;
+                    u.insert_seen = true;
+                } else if (u.insert != bytes) {
+                    u.insert_conflict = true;
+                }
             }
             r0 = sc_unknown();
             r0.taint = det ? 1 : 0;
@@ -1544,7 +1565,10 @@ struct Verifier {
     int run() {
         out->info.assign(n, InsnInfo());
         out->map_use.assign(n_maps, MapUse());
-        for (u32 m = 0; m < n_maps && m < GX_MAX_MAPS; m++) out->map_use[m].op.assign((maps[m].value_size + 3) / 4, UC_NONE);
+        for (u32 m = 0; m < n_maps && m < GX_MAX_MAPS; m++) {
+            out->map_use[m].op.assign((maps[m].value_size + 3) / 4, UC_NONE);
+            out->map_use[m].merge_op.assign((maps[m].value_size + 3) / 4, UC_NONE);
+        }
         if (n == 0 || n > GX_MAX_INSNS) return fail(0, "program length %u not in [1, %d]", n, GX_MAX_INSNS);
         if (opts.ctx_size < 8 || opts.ctx_size > GX_MAX_CTX || opts.ctx_size % 8)
             return fail(0, "ctx_size %u invalid", opts.ctx_size);

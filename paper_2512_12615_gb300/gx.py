@@ -125,6 +125,8 @@ _SIGS = {
                              ctypes.POINTER(SimtSpec), ctypes.POINTER(SimtReport), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_jit_check_simt": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                                 ctypes.POINTER(SimtSpec), ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_merge_ops": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts), u32,
+                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(u32), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
                              ctypes.POINTER(ProgOpts), ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                              ctypes.c_size_t]),
@@ -273,6 +275,28 @@ def jit_check_simt(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, 
                                  ctypes.byref(spec), log, 1 << 20)
     del keep
     return rc, log.value.decode()
+
+
+# gx_merge_ops word codes
+MERGE_NONE, MERGE_ADD, MERGE_OR, MERGE_AND, MERGE_XOR, MERGE_MAX, MERGE_MIN = range(7)
+MERGE_W8 = 0x10
+
+
+def merge_ops(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, map_index: int,
+              insn_budget: int = 0) -> Tuple[int, np.ndarray, Optional[bytes], str]:
+    """Host-only (gx_merge_ops): (status, per-4-byte-word merge codes, the hash insert's constant
+    bytes or None when the program never inserts, log)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    specs = _specs(map_specs)
+    opts = ProgOpts(ctx_size, 1, insn_budget, 0, 0)
+    vs = int(map_specs[map_index]["value_size"]) if 0 <= map_index < len(map_specs) else 0
+    ops = np.zeros(max(1, (vs + 3) // 4), dtype=np.uint8)
+    ins = np.zeros(max(1, vs), dtype=np.uint8)
+    has = u32(0)
+    log = ctypes.create_string_buffer(1024)
+    rc = lib().gx_merge_ops(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts), map_index,
+                            ops.ctypes.data, ins.ctypes.data, ctypes.byref(has), log, 1024)
+    return rc, ops[:(vs + 3) // 4], (ins[:vs].tobytes() if has.value else None), log.value.decode()
 
 
 PROG_JIT = 1
