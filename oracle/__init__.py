@@ -220,3 +220,104 @@ def run_warps(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_siz
 
 def maps_from_specs(specs: Sequence[dict]) -> List[Map]:
     return [Map.from_spec(s) for s in specs]
+
+
+# ------------------------------------------------------------------ several parts at once
+def _combine(op: str, width: int, start: int, vals: List[int]) -> int:
+    """One value word merged over the parts that hold it, from its starting value `start`."""
+    mask = (1 << (8 * width)) - 1
+    r = start
+    for v in vals:
+        if op == "add":
+            r = (r + v - start) & mask
+        elif op == "xor":
+            r ^= v ^ start
+        elif op == "or":
+            r |= v
+        elif op == "and":
+            r &= v
+        elif op == "max":
+            r = max(r, v)
+        elif op == "min":
+            r = min(r, v)
+        else:
+            raise ValueError(op)
+    return r
+
+
+def _merge_value(words, free: List[int], start: bytes, vals: List[bytes]) -> bytes:
+    """vals merged word by word; `free` lists the bytes no update reaches."""
+    out = bytearray(vals[0])
+    for v in vals[1:]:  # bytes no update reaches are the same in every part
+        for b in free:
+            if v[b] != out[b]:
+                raise ValueError(f"byte {b} differs between parts but no update reaches it")
+    for off, width, op in words:
+        r = _combine(op, width, int.from_bytes(start[off:off + width], "little"),
+                     [int.from_bytes(v[off:off + width], "little") for v in vals])
+        out[off:off + width] = r.to_bytes(width, "little")
+    return bytes(out)
+
+
+def run_parallel(prog: np.ndarray, specs: Sequence[dict], events: np.ndarray, ctx_size: int, merge: Sequence,
+                 *, threads: Optional[int] = None, event_idx_base: int = 0, budget: int = 0,
+                 init: Optional[Sequence[Optional[bytes]]] = None) -> Tuple[list, int]:
+    """`run` over `threads` contiguous parts of `events` at once, each part with maps of its
+    own and its global event base, merged afterwards.  Equal to `run` over the whole batch
+    when the program changes map values only by commutative updates (the deterministic
+    reading of Sec. 4.4.3), which makes the parts' order irrelevant.
+
+    merge: per map, how its values combine, from the caller's knowledge of the program:
+    {"words": [(byte offset, width, op)], "insert": bytes of a new hash key} with op one of
+    add, xor, or, and, max, min (None for ring buffers).  init: per array map, the starting
+    contents (None = zeros).  Returns (snapshots, executed instructions): per map the
+    array bytes (max_entries x value_size), the {key: value} dict, or (records, dropped)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    raw = np.ascontiguousarray(events).view(np.uint8).reshape(-1)
+    n = raw.size // ctx_size
+    t = max(1, min(threads or os.cpu_count() or 1, n or 1))
+    cuts = [n * j // t for j in range(t + 1)]
+
+    def part(j):
+        maps = maps_from_specs(specs)
+        for m, v in zip(maps, init or [None] * len(maps)):
+            if v is not None:
+                for k in range(m.max_entries):
+                    m.update(k.to_bytes(4, "little"), v[k * m.value_size:(k + 1) * m.value_size])
+        _, count = run(prog, maps, raw[cuts[j] * ctx_size:cuts[j + 1] * ctx_size], ctx_size,
+                       event_idx_base=event_idx_base + cuts[j], budget=budget)
+        snaps = []
+        for m in maps:
+            if m.type == MAP_ARRAY:
+                snaps.append(m.array_values())
+            elif m.type == MAP_HASH:
+                snaps.append(m.hash_items())
+            else:
+                snaps.append(m.ringbuf_records())
+        return snaps, count
+
+    with ThreadPoolExecutor(max_workers=t) as pool:  # the C interpreter runs without the GIL
+        parts = list(pool.map(part, range(t)))
+    out = []
+    for i, spec in enumerate(specs):
+        copies = [p[0][i] for p in parts]
+        if spec["type"] == MAP_RINGBUF:  # the parts are in event order and so are their records
+            out.append(([r for recs, _ in copies for r in recs], sum(d for _, d in copies)))
+            continue
+        words = merge[i]["words"]
+        free = [b for b in range(spec["value_size"]) if not any(o <= b < o + w for o, w, _ in words)]
+        if spec["type"] == MAP_ARRAY:
+            vs = spec["value_size"]
+            start = init[i] if init and init[i] is not None else bytes(spec["max_entries"] * vs)
+            arr = np.zeros((spec["max_entries"], vs), dtype=np.uint8)
+            for k in range(spec["max_entries"]):
+                vals = [c[k].tobytes() for c in copies]
+                arr[k] = np.frombuffer(_merge_value(words, free, start[k * vs:(k + 1) * vs], vals), dtype=np.uint8)
+            out.append(arr)
+        else:
+            merged = {}
+            for key in {k for c in copies for k in c}:
+                merged[key] = _merge_value(words, free, merge[i]["insert"], [c[key] for c in copies if key in c])
+            out.append(merged)
+    return out, sum(c for _, c in parts)
