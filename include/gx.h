@@ -335,8 +335,8 @@ int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec
  * verified in deterministic mode whatever opts->deterministic says: that mode is what makes
  * the merge exact.  word_ops (ceil(value_size / 4) entries) receives, per 4-byte word of a
  * value, the update that changes it: GX_MERGE_NONE (never changed) or GX_MERGE_ADD / _OR /
- * _AND / _XOR / _MAX / _MIN, with GX_MERGE_W8 set when the update is 64 bits wide (both
- * words of the 8-byte pair carry it).  insert_value (value_size bytes, nullable) receives
+ * _AND / _XOR / _MAX / _MIN, with GX_MERGE_W8 set on both words of an 8-byte pair that a
+ * 64-bit ADD, MAX or MIN updates (bitwise operations merge per 4-byte word at any width).  insert_value (value_size bytes, nullable) receives
  * the constant bytes a hash insert writes and *has_insert (nullable) whether the program
  * inserts into this map at all.  A word merges over the copies that hold the entry, with i
  * its starting value (the array's contents before the runs; insert_value for a new hash
@@ -344,8 +344,8 @@ int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec
  * MIN (unsigned) are the operation over the copies.  Hash maps merge as the union of their
  * keys; ring buffers as the records of all copies ordered by event index (no ops needed).
  * Returns 0, GX_E_VERIFY (rejected in deterministic mode) or GX_EINVAL (bad arguments, or
- * copies that cannot be merged: a word updated at two widths, or inserts of different
- * constants; `log` says which).
+ * copies that cannot be merged: inserts of different constants; `log` says which).  A
+ * program that adds to the same bytes at two widths is rejected (GX_E_VERIFY).
  */
 #define GX_MERGE_NONE 0u
 #define GX_MERGE_ADD 1u

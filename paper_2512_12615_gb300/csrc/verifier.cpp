@@ -23,7 +23,8 @@
  *   Sec. 4.4.3): values read back from maps, fetched by atomics or returned by updates
  *   are tainted and may not reach branch conditions, R0 at exit, map keys, stored map
  *   values, ring-buffer payloads or pointer offsets; map values change only through
- *   ADD/OR/AND/XOR atomics without fetch or the atomic max/min helpers; updates must be
+ *   ADD/OR/AND/XOR atomics without fetch or the atomic max/min helpers, adds to the same
+ *   bytes at one width (a 32-bit add drops the carry a 64-bit add keeps); updates must be
  *   NOEXIST inserts of constant bytes; deletes, XCHG and CMPXCHG on map memory are
  *   refused.  Under these rules the final map state, the set of ring-buffer records and
  *   every R0 are the same for every order in which the events run.
@@ -422,7 +423,7 @@ struct Verifier {
     /* deterministic mode: which atomic operation class updates which bytes of each map */
     struct OpRange {
         s64 lo, hi;
-        int cls;
+        int cls, size;
     };
     std::vector<OpRange> op_ranges[GX_MAX_MAPS];
     u32 next_id = 1;
@@ -685,14 +686,20 @@ struct Verifier {
     int note_update(u32 pc, const Reg &p, int off, int size, int cls) {
         if (!opts.deterministic) return GX_OK;
         s64 lo = p.smin + off, hi = p.smax + off + size;
-        for (const OpRange &r : op_ranges[p.map])
+        for (const OpRange &r : op_ranges[p.map]) {
             if (r.cls != cls && lo < r.hi && r.lo < hi)
                 return fail(pc, "map memory updated by two different atomic operations (order-dependent)");
-        op_ranges[p.map].push_back(OpRange{lo, hi, cls});
+            /* a 32-bit add drops the carry a 64-bit add keeps: mixed, the order decides the result */
+            if (cls == OPC_ADD && r.cls == OPC_ADD && r.size != size && lo < r.hi && r.lo < hi)
+                return fail(pc, "map memory added to at two widths (order-dependent)");
+        }
+        op_ranges[p.map].push_back(OpRange{lo, hi, cls, size});
         /* the words this update may change, for merging copies (8-byte updates are 8-aligned) */
         static_assert(OPC_ADD == UC_ADD && OPC_MIN == UC_MIN, "one numbering for update classes");
         MapUse &u = out->map_use[p.map];
-        const uint8_t code = (uint8_t)(cls | (size == 8 ? UC_W8 : 0));
+        /* bitwise operations merge per 4-byte word whatever their width; ADD, MAX and MIN by width */
+        const bool wide = size == 8 && (cls == OPC_ADD || cls == OPC_MAX || cls == OPC_MIN);
+        const uint8_t code = (uint8_t)(cls | (wide ? UC_W8 : 0));
         const s64 a = std::max<s64>(lo, 0) & ~(s64)(size - 1), b = (hi + size - 1) & ~(s64)(size - 1);
         for (s64 w = a / 4; w < (b + 3) / 4 && w < (s64)u.merge_op.size(); w++) {
             if (u.merge_op[(size_t)w] == UC_NONE) u.merge_op[(size_t)w] = code;

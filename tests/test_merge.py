@@ -113,7 +113,7 @@ def test_nonzero_insert_constant():
     specs = [dict(type=1, key_size=8, value_size=16, max_entries=64)]
     prog = assemble(lines).prog()
     rc, ops, insert, _ = gx.merge_ops(prog, specs, 16, 0)
-    assert rc == 0 and list(ops) == [0x11, 0x11, 0x14, 0x14]
+    assert rc == 0 and list(ops) == [0x11, 0x11, 0x04, 0x04]  # the XOR merges per 4-byte word
     assert insert == (5).to_bytes(8, "little") + (2**64 - 16).to_bytes(8, "little")
     ev = np.random.default_rng(5).integers(0, 2**63, size=(5_000, 2), dtype=np.uint64)
     assert_merge_equals_whole(prog, specs, 16, ev, [0, 1_000, 2_500, 5_000])
@@ -154,13 +154,17 @@ def test_merge_codes_and_refusals():
     assert rc == 0 and list(ops) == [gx.MERGE_W8 | gx.MERGE_ADD] * 2 + [gx.MERGE_W8 | gx.MERGE_MAX] * 2
     assert insert == bytes(16)
     assert gx.merge_ops(prog, specs, cs, 1)[2] is None  # the tally is never inserted into
-    # a word added at two widths
+    # a word added at two widths is order-dependent: refused by deterministic verification
     arr = [dict(type=2, key_size=4, value_size=8, max_entries=1)]
     look = ["st4 r10 -4 0", "ld_map r1 0", "mov r2 r10", "add r2 -4", "call map_lookup_elem", "jeq r0 0 out",
             "mov r1 1"]
     rc, _, _, log = gx.merge_ops(assemble(look + ["atomic8 add r0 0 r1", "atomic4 add r0 0 r1", "out:", "mov r0 0",
                                                   "exit"]).prog(), arr, 16, 0)
-    assert rc == gx.EINVAL and "two widths" in log
+    assert rc == gx.E_VERIFY and "two widths" in log
+    # bitwise operations at two widths merge per 4-byte word
+    rc, ops, _, log = gx.merge_ops(assemble(look + ["atomic8 or r0 0 r1", "atomic4 or r0 0 r1", "out:", "mov r0 0",
+                                                    "exit"]).prog(), arr, 16, 0)
+    assert rc == 0 and list(ops) == [gx.MERGE_OR, gx.MERGE_OR], log
     # inserts of two different constants
     hs = [dict(type=1, key_size=8, value_size=8, max_entries=4)]
     ins = ["st8 r10 -8 1", "st8 r10 -16 {}", "ld_map r1 0", "mov r2 r10", "add r2 -8", "mov r3 r10", "add r3 -16",

@@ -294,3 +294,29 @@ def test_rejects_delete_on_an_insert_only_hash_map():
 def test_rejects_bad_map_flags(spec):
     rc, log = gx.verify(assemble(["mov r0 0", "exit"]).prog(), [spec], 32)
     assert rc == gx.EINVAL and "invalid map spec" in log
+
+
+def test_det_rejects_adds_at_two_widths():
+    """A 32-bit add drops the carry a 64-bit add keeps.  On one word, two events in the two
+    orders leave different values (the oracle shows it), so deterministic mode refuses
+    adds to the same bytes at two widths; bitwise operations at two widths commute."""
+    import oracle as O
+
+    body = ["ldx8 r3 r6 0", "jeq r3 0 wide", "mov r3 1", "atomic4 add r7 0 r3", "ja out", "wide:", "mov r3 1",
+            "atomic8 add r7 0 r3"]
+    lines = ["mov r6 r1"] + VALUE + ["mov r7 r0"] + body + ["out:", "mov r0 0", "exit"]
+    ok(lines, [ARRAY])
+    rejected(lines, [ARRAY], det=True, why="two widths")
+    ok(["mov r6 r1"] + VALUE + ["mov r7 r0"] + [b.replace("add", "or") for b in body] + ["out:", "mov r0 0", "exit"],
+       [ARRAY], det=True)
+    ok(VALUE + ["mov r3 1", "atomic8 add r0 0 r3", "atomic4 add r0 8 r3", "out:", "mov r0 0", "exit"],
+       [dict(ARRAY, value_size=16)], det=True)  # disjoint words
+    # the word starts at 2^32 - 1: add32 then add64 gives 1, add64 then add32 gives 2^32 + 1
+    prog = assemble(lines).prog()
+    finals = []
+    for order in ([1, 0], [0, 1]):
+        maps = O.maps_from_specs([ARRAY])
+        maps[0].update((0).to_bytes(4, "little"), (2**32 - 1).to_bytes(8, "little"))  # the key LOOKUP uses
+        O.run(prog, maps, np.array([[order[0], 0], [order[1], 0]], dtype=np.uint64), 16)
+        finals.append(int(maps[0].array_u64()[0, 0]))
+    assert finals == [1, 2**32 + 1]
