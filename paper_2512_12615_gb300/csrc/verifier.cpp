@@ -25,7 +25,7 @@
  *   values, ring-buffer payloads or pointer offsets; map values change only through
  *   ADD/OR/AND/XOR atomics without fetch or the atomic max/min helpers, adds to the same
  *   bytes at one width (a 32-bit add drops the carry a 64-bit add keeps); updates must be
- *   NOEXIST inserts of constant bytes; deletes, XCHG and CMPXCHG on map memory are
+ *   NOEXIST inserts of constant bytes, one constant per map; deletes, XCHG and CMPXCHG on map memory are
  *   refused.  Under these rules the final map state, the set of ring-buffer records and
  *   every R0 are the same for every order in which the events run.
  *   SIMT mode (gx_verify_simt; the warp-uniformity pass and per-hook budgets of Sec. 4.4.1
@@ -1478,8 +1478,9 @@ struct Verifier {
                 if (!u.insert_seen) {
                     u.insert = bytes;
                     u.insert_seen = true;
-                } else if (u.insert != bytes) {
+                } else if (u.insert != bytes) { /* two events inserting one key: the first one's bytes stay */
                     u.insert_conflict = true;
+                    return fail(pc, "inserts of different constants into one map (order-dependent)");
                 }
             }
             r0 = sc_unknown();

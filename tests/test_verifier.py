@@ -320,3 +320,16 @@ def test_det_rejects_adds_at_two_widths():
         O.run(prog, maps, np.array([[order[0], 0], [order[1], 0]], dtype=np.uint64), 16)
         finals.append(int(maps[0].array_u64()[0, 0]))
     assert finals == [1, 2**32 + 1]
+
+
+def test_det_rejects_inserts_of_different_constants():
+    """Two events inserting one key with NOEXIST: the first one's bytes stay, so two
+    different inserted constants make the result order-dependent."""
+    ins = ["st8 r10 -8 1", "st8 r10 -16 {}", "ld_map r1 0", "mov r2 r10", "add r2 -8", "mov r3 r10", "add r3 -16",
+           "mov r4 1", "call map_update_elem"]
+    hs = [dict(HASH, value_size=8)]
+    same = [x.format(7) for x in ins] * 2 + ["mov r0 0", "exit"]
+    two = [x.format(0) for x in ins] + [x.format(7) for x in ins] + ["mov r0 0", "exit"]
+    ok(same, hs, det=True)
+    ok(two, hs)
+    rejected(two, hs, det=True, why="different constants")
