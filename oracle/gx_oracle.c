@@ -301,6 +301,7 @@ typedef struct {
 typedef struct {
     region r[MAX_REGIONS];
     int n;
+    int strict_align; /* or_run_flags OR_STRICT_ALIGN: instruction accesses must be naturally aligned */
 } regions;
 
 static void grant(regions *g, uint8_t *base, uint64_t size, int writable) {
@@ -466,6 +467,7 @@ typedef struct {
     uint64_t event_idx;
     regions *g;
     region granted; /* the region the last helper call granted (size 0: none) */
+    int strict_align;
 } hctx;
 
 static or_map *map_arg(const hctx *h, uint64_t v) {
@@ -582,7 +584,7 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
     case 0x10000: /* atomic_max_u64(ptr, v) */
     case 0x10001: { /* atomic_min_u64(ptr, v) */
         uint8_t *p = check(g, R[1], 8, 1);
-        if (!p) return OR_EFAULT;
+        if (!p || (g->strict_align && R[1] % 8)) return OR_EFAULT;
         uint64_t cur = load_le(p, 8);
         if (id == 0x10000 ? R[2] > cur : R[2] < cur) store_le(p, 8, R[2]);
         r0 = 0;
@@ -649,8 +651,9 @@ static int ins_ldx(uint64_t *R, const regions *g, uint8_t op, int dst, int src, 
     uint8_t mode = op & 0xE0;
     int sz = size_of(op);
     if (dst == 10 || (mode != 0x60 && mode != 0x80) || (mode == 0x80 && sz == 8)) return OR_EINVAL;
-    uint8_t *p = check(g, R[src] + (uint64_t)(int64_t)off, (uint64_t)sz, 0);
-    if (!p) return OR_EFAULT;
+    uint64_t a = R[src] + (uint64_t)(int64_t)off;
+    uint8_t *p = check(g, a, (uint64_t)sz, 0);
+    if (!p || (g->strict_align && a % (uint64_t)sz)) return OR_EFAULT;
     uint64_t v = load_le(p, sz);
     R[dst] = mode == 0x80 ? sext(v, 8 * sz) : v;
     return OR_OK;
@@ -664,6 +667,7 @@ static int ins_store(uint64_t *R, const regions *g, uint8_t op, int dst, int src
     uint8_t cls = op & 7, mode = op & 0xE0;
     int sz = size_of(op);
     uint64_t a = store_addr(R, dst, off);
+    if (g->strict_align && a % (uint64_t)sz) return OR_EFAULT;
     if (mode == 0x60) {
         uint8_t *p = check(g, a, (uint64_t)sz, 1);
         if (!p) return OR_EFAULT;
@@ -708,6 +712,7 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
     memset(R, 0, sizeof R);
     memset(stack, 0, sizeof stack);
     g.n = 0;
+    g.strict_align = h->strict_align;
     grant(&g, ctx, ctx_size, 0);
     grant(&g, stack, STACK_BYTES, 1);
     h->g = &g;
@@ -777,12 +782,17 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
  * r0_out (nullable): R0 per event.  insn_count (nullable): total executed instructions
  * (a 64-bit immediate load counts once).  budget: per-event instruction cap (0 = 2^20).
  * Returns 0 or the first error; *bad_event = the index of the event that failed.
+ * or_run_flags: OR_STRICT_ALIGN also stops with OR_EFAULT at a load, store or atomic (the
+ * max / min helpers included) whose address is not a multiple of its size, the engine's
+ * reading that device accesses are naturally aligned; or_run leaves alignment free.
  */
-int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
-           uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out, uint64_t *insn_count,
-           uint64_t budget, uint64_t *bad_event) {
+#define OR_STRICT_ALIGN 1u
+int or_run_flags(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
+                 uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out,
+                 uint64_t *insn_count, uint64_t budget, uint64_t *bad_event, uint32_t flags) {
     hctx h;
     memset(&h, 0, sizeof h);
+    h.strict_align = (flags & OR_STRICT_ALIGN) != 0;
     h.maps = maps;
     h.n_maps = n_maps;
     uint64_t count = 0;
@@ -801,6 +811,13 @@ int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_ma
     }
     if (insn_count) *insn_count = count;
     return OR_OK;
+}
+
+int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
+           uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out, uint64_t *insn_count,
+           uint64_t budget, uint64_t *bad_event) {
+    return or_run_flags(insns, n_insns, maps, n_maps, events, n_events, ctx_size, event_idx_base, r0_out, insn_count,
+                        budget, bad_event, 0);
 }
 
 /* ------------------------------------------------------------------ one warp, in lockstep */
@@ -986,6 +1003,7 @@ static int run_warp(const uint64_t *insns, uint32_t n, hctx *h, lane *L, uint32_
         memset(L[i].R, 0, sizeof L[i].R);
         memset(L[i].stack, 0, sizeof L[i].stack);
         L[i].g.n = 0;
+        L[i].g.strict_align = h->strict_align;
         grant(&L[i].g, L[i].ctx, ctx_size, 0);
         grant(&L[i].g, L[i].stack, STACK_BYTES, 1);
         L[i].R[1] = (uint64_t)(uintptr_t)L[i].ctx;

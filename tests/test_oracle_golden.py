@@ -82,3 +82,36 @@ def test_insn_count_is_exact():
     prog = assemble(["mov r0 0", "mov r2 1", "l:", "add r0 r2", "add r2 1", "jle r2 10 l", "exit"]).prog()
     _, count = O.run(prog, [], np.zeros((1, 2), dtype=np.uint64), 16)
     assert count == 2 + 30 + 1
+
+
+@pytest.mark.parametrize("lines,misaligned", [
+    (["st8 r10 -8 0", "ldx4 r0 r10 -6", "exit"], True),
+    (["st8 r10 -8 0", "ldx4 r0 r10 -4", "exit"], False),
+    (["st8 r10 -8 0", "st2 r10 -7 1", "mov r0 0", "exit"], True),
+    (["st8 r10 -8 0", "mov r1 1", "atomic4 add r10 -6 r1", "mov r0 0", "exit"], True),
+    (["ldx2 r0 r1 3", "exit"], True),
+    (["ldx1 r0 r1 3", "exit"], False),
+])
+def test_strict_alignment(lines, misaligned):
+    """OR_STRICT_ALIGN: an access whose address is not a multiple of its size faults (the
+    engine's reading that device accesses are naturally aligned); by default alignment is free."""
+    ev = np.zeros((1, 2), dtype=np.uint64)
+    prog = assemble(lines).prog()
+    O.run(prog, [], ev, 16)
+    if misaligned:
+        with pytest.raises(O.OracleError) as e:
+            O.run(prog, [], ev, 16, strict_align=True)
+        assert e.value.rc == O.EFAULT
+    else:
+        O.run(prog, [], ev, 16, strict_align=True)
+
+
+def test_strict_alignment_of_the_max_helper():
+    specs = [dict(type=2, key_size=4, value_size=16, max_entries=1)]
+    look = ["st4 r10 -4 0", "ld_map r1 0", "mov r2 r10", "add r2 -4", "call map_lookup_elem", "jeq r0 0 out",
+            "mov r1 r0", "add r1 {}", "mov r2 5", "call atomic_max_u64", "out:", "mov r0 0", "exit"]
+    ev = np.zeros((1, 2), dtype=np.uint64)
+    O.run(assemble([x.format(8) for x in look]).prog(), O.maps_from_specs(specs), ev, 16, strict_align=True)
+    with pytest.raises(O.OracleError) as e:
+        O.run(assemble([x.format(4) for x in look]).prog(), O.maps_from_specs(specs), ev, 16, strict_align=True)
+    assert e.value.rc == O.EFAULT

@@ -3,7 +3,8 @@
 The engine runs verified programs without run-time bounds checks, so the proof is what
 keeps device memory safe (Sec. 4.4: memory safety, bounded loops, typed access).  The
 oracle checks every access against the regions an event may touch (its ctx read-only,
-its stack, looked-up values, its ring reservations) and stops with EFAULT or EINVAL
+its stack, looked-up values, its ring reservations), and in strict-alignment mode that
+every load, store and atomic is naturally aligned, and stops with EFAULT or EINVAL
 otherwise.  So: every random program the verifier accepts must run through the oracle
 without either, over random events.
 
@@ -168,7 +169,7 @@ def test_accepted_programs_never_fault():
         ev = rng.integers(0, 2**64 - 1, size=(64, CTX // 8), dtype=np.uint64, endpoint=True)
         ev[::3] &= np.uint64(0xFF)  # small values take the checked branches too
         try:
-            O.run(prog, O.maps_from_specs(SPECS), ev, CTX)
+            O.run(prog, O.maps_from_specs(SPECS), ev, CTX, strict_align=True)
         except O.OracleError as e:
             assert e.rc == O.EBUDGET, (i, e, lines)
     assert accepted >= 300, accepted
