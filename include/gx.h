@@ -321,12 +321,23 @@ int gx_verify_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *m
  * sm_103a without loading it (NVRTC must be available; no device needed).  In that form the
  * 32 lanes of a warp run the handler over 32 consecutive events; helper calls, and stores
  * and atomics outside the lane's stack, run on the warp's first valid lane with their
- * results broadcast; the warp helpers reduce over the valid lanes.  No entry point loads
- * this form yet.  0, GX_E_VERIFY, GX_E_NODEV (no runtime compiler) or GX_E_CUDA (compile
+ * results broadcast; the warp helpers reduce over the valid lanes.  gx_verify_load_simt
+ * loads it.  0, GX_E_VERIFY, GX_E_NODEV (no runtime compiler) or GX_E_CUDA (compile
  * error); `log` explains.
  */
 int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
                       const gx_prog_opts *opts, const gx_simt_spec *simt, char *log, size_t log_len);
+/*
+ * SIMT-verify a program, compile its warp-level form (as gx_jit_check_simt) and load it.
+ * opts->flags must be GX_PROG_JIT: the form exists only as specialised code.  A run of the
+ * program treats each 32 consecutive events (from the batch's first) as one warp: the lanes
+ * take one path, and shared state changes once per warp.  A batch or server that would run
+ * it through the interpreter refuses it (GX_EINVAL).  This form has not yet run on a GPU.
+ * Returns as gx_verify_load.
+ */
+int gx_verify_load_simt(gx_ctx *ctx, const uint64_t *insns, uint32_t n_insns, gx_map *const *maps, uint32_t n_maps,
+                        const gx_prog_opts *opts, const gx_simt_spec *simt, gx_prog **out, char *log,
+                        size_t log_len);
 
 /*
  * Host only: how to merge copies of map `map_index` that several engines (one per GPU,

@@ -646,6 +646,84 @@ int gx_prog_destroy(gx_prog *p) {
     return GX_OK;
 }
 
+/* upload a verified program's image (header, map table, micro-ops) and take its map references */
+static int upload_program(gx_ctx *c, gx_prog *p, gx_map *const *maps, uint32_t n_maps) {
+    for (uint32_t i = 0; i < n_maps; i++) {
+        p->maps.push_back(maps[i]);
+        maps[i]->refs++;
+    }
+    std::vector<gx_dmap> descs;
+    for (auto *m : p->maps) descs.push_back(m->d);
+    uint64_t img_guess = round_up(sizeof(gx_dprog_hdr) + descs.size() * sizeof(gx_dmap) + p->uops.size() * 8, 16);
+    uint64_t stats_off = round_up(img_guess, 256);
+    p->dbytes = stats_off + 256;
+    int rc = dalloc(c, p->dbytes, &p->dmem);
+    if (rc) {
+        for (auto *m : p->maps) map_release(m);
+        return rc;
+    }
+    p->dstats = (unsigned long long *)((uint8_t *)p->dmem + stats_off);
+    std::vector<uint8_t> img = build_image(p, descs, p->dstats);
+    p->image_bytes = (uint32_t)img.size();
+    if (p->image_bytes > GX_MAX_IMAGE) rc = GX_E2BIG;
+    else if (cudaMemcpy(p->dmem, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemset(p->dstats, 0, 256) != cudaSuccess)
+        rc = GX_E_CUDA;
+    if (rc) {
+        dfree(c, p->dmem, p->dbytes);
+        for (auto *m : p->maps) map_release(m);
+        return rc;
+    }
+    c->live++;
+    return GX_OK;
+}
+
+int gx_verify_load_simt(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *maps, uint32_t n_maps,
+                        const gx_prog_opts *opts, const gx_simt_spec *simt, gx_prog **out, char *log,
+                        size_t log_len) {
+    if (!c || !insns || !opts || !simt || !out || (n_maps && !maps) || simt->reserved) return GX_EINVAL;
+    if (opts->flags != GX_PROG_JIT) return GX_EINVAL; /* the warp-level form exists only as specialised code */
+    if (opts->ctx_size < 8 || opts->ctx_size > GX_MAX_CTX) return GX_EINVAL;
+    *out = nullptr;
+    std::vector<gx_map_spec> specs(n_maps);
+    for (uint32_t i = 0; i < n_maps; i++) {
+        if (!maps[i] || maps[i]->ctx != c) return GX_EINVAL;
+        specs[i] = maps[i]->spec;
+    }
+    const SimtIn in = simt_in(*simt, opts->ctx_size);
+    VerifyOut v;
+    int rc = verify_program(insns, n, specs.data(), n_maps, *opts, v, &in);
+    std::string msg = v.log;
+    gx_prog *p = nullptr;
+    if (rc == GX_OK) {
+        p = new gx_prog();
+        p->ctx = c;
+        p->opts = *opts;
+        /* no micro-ops: the interpreter never runs this form (batches and servers refuse to) */
+        p->jp.insns.assign(insns, insns + n);
+        p->jp.info = v.info;
+        p->jp.maps = specs;
+        p->jp.use = v.map_use;
+        p->jp.ctx_size = opts->ctx_size;
+        p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        p->jp.warp = true;
+        rc = jit_build({&p->jp}, p->jk, msg);
+        p->jit = rc == GX_OK;
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, msg.size());
+        memcpy(log, msg.data(), k);
+        log[k] = 0;
+    }
+    if (rc == GX_OK) rc = upload_program(c, p, maps, n_maps);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return GX_OK;
+}
+
 uint32_t gx_prog_uops(const gx_prog *p) { return p ? (uint32_t)p->uops.size() : 0; }
 
 /* ---------------------------------------------------------------- runs */

@@ -209,7 +209,11 @@ static int batch_jit(gx_batch *b) {
     b->jit = !b->items.empty();
     for (auto &it : b->items)
         if (!it.prog->jit) b->jit = false;
-    if (!b->jit) return GX_OK;
+    if (!b->jit) {
+        for (auto &it : b->items)
+            if (it.prog->jp.warp) return GX_EINVAL; /* a warp-level program exists only as specialised code */
+        return GX_OK;
+    }
     std::vector<const gx::JitProgram *> progs;
     b->slots.clear();
     for (auto &it : b->items)
@@ -439,6 +443,12 @@ int gx_server_create(gx_ctx *c, const gx_server_opts *o, gx_server **out) {
                 progs.push_back(&p->jp);
             }
         }
+        if (!all_jit && !opts.plain)
+            for (auto &ps : s->prog_slot)
+                if (ps.first->jp.warp) { /* a warp-level program exists only as specialised code */
+                    delete s;
+                    return GX_EINVAL;
+                }
         if (all_jit && !opts.plain) {
             std::string log;
             int rc = gx::jit_build(progs, s->jk, log);

@@ -130,6 +130,9 @@ _SIGS = {
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
                              ctypes.POINTER(ProgOpts), ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p,
                              ctypes.c_size_t]),
+    "gx_verify_load_simt": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
+                                  ctypes.POINTER(ProgOpts), ctypes.POINTER(SimtSpec), ctypes.POINTER(ctypes.c_void_p),
+                                  ctypes.c_char_p, ctypes.c_size_t]),
     "gx_prog_destroy": (i32, [ctypes.c_void_p]),
     "gx_prog_uops": (u32, [ctypes.c_void_p]),
     "gx_run_batch": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p]),
@@ -391,16 +394,27 @@ class Map:
 
 class Program:
     def __init__(self, ctx: Context, insns: np.ndarray, maps: Sequence[Map], ctx_size: int,
-                 deterministic: bool = False, insn_budget: int = 0, jit: bool = False) -> None:
+                 deterministic: bool = False, insn_budget: int = 0, jit: bool = False,
+                 simt: Optional[dict] = None) -> None:
+        """simt: load the warp-level form (gx_verify_load_simt) with these gx_simt_spec fields:
+        uniform (ctx_size flags) and optionally max_insns, max_helper_calls, max_mem_ops;
+        it needs jit=True."""
         insns = np.ascontiguousarray(insns, dtype=np.uint64)
         arr = (ctypes.c_void_p * max(1, len(maps)))(*[m.h for m in maps])
         opts = ProgOpts(ctx_size, int(deterministic), insn_budget, PROG_JIT if jit else 0, 0)
         log = ctypes.create_string_buffer(8192)
         h = ctypes.c_void_p()
-        rc = lib().gx_verify_load(ctx.h, insns.ctypes.data, insns.size, arr, len(maps), ctypes.byref(opts),
-                                  ctypes.byref(h), log, 8192)
+        if simt is None:
+            rc = lib().gx_verify_load(ctx.h, insns.ctypes.data, insns.size, arr, len(maps), ctypes.byref(opts),
+                                      ctypes.byref(h), log, 8192)
+        else:
+            spec, keep = _simt_spec(ctx_size, simt.get("uniform"), simt.get("max_insns", 0),
+                                    simt.get("max_helper_calls", 0), simt.get("max_mem_ops", 0))
+            rc = lib().gx_verify_load_simt(ctx.h, insns.ctypes.data, insns.size, arr, len(maps), ctypes.byref(opts),
+                                           ctypes.byref(spec), ctypes.byref(h), log, 8192)
+            del keep
         if rc:
-            raise GxError(rc, "gx_verify_load", log.value.decode())
+            raise GxError(rc, "gx_verify_load" if simt is None else "gx_verify_load_simt", log.value.decode())
         self.h, self.ctx, self.maps, self.ctx_size = h, ctx, list(maps), ctx_size
 
     def destroy(self) -> None:
