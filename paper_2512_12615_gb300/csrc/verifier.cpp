@@ -25,9 +25,9 @@
  *   values, ring-buffer payloads or pointer offsets; map values change only through
  *   ADD/OR/AND/XOR atomics without fetch or the atomic max/min helpers, adds to the same
  *   bytes at one width (a 32-bit add drops the carry a 64-bit add keeps); updates must be
- *   NOEXIST inserts of constant bytes, one constant per map; deletes, XCHG and CMPXCHG on map memory are
- *   refused.  Under these rules the final map state, the set of ring-buffer records and
- *   every R0 are the same for every order in which the events run.
+ *   NOEXIST inserts of constant bytes, one constant per map; deletes, XCHG and CMPXCHG on
+ *   map memory are refused.  Under these rules the final map state, the set of ring-buffer
+ *   records and every R0 are the same for every order in which the events run.
  *   SIMT mode (gx_verify_simt; the warp-uniformity pass and per-hook budgets of Sec. 4.4.1
  *   and Sec. 5.3): a second mark, lane-varying, starts at the ctx bytes not declared
  *   warp-uniform and flows like the taint through registers, spills and stack bytes.  A
@@ -62,7 +62,6 @@ const size_t MAX_STATES_TOTAL = 16384;
 
 enum RT : uint8_t { NI = 0, SC, CTX, STK, CMAP, MV, MVN, RB, RBN };
 const uint8_t ST_LV = 0x40, ST_TAINT = 0x80;
-
 
 const char *rt_name(int t) {
     static const char *n[] = {"uninit", "scalar", "ctx", "stack", "map", "map_value", "map_value_or_null",
