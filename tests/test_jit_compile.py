@@ -237,3 +237,54 @@ def test_warp_form_of_random_handlers_compiles():
 def test_warp_form_needs_simt_verification():
     rc, log = gx.jit_check_simt(assemble(["ldx8 r0 r1 0", "exit"]).prog(), [], 16, [False] * 16)
     assert rc == gx.E_VERIFY and "lane-varying" in log
+
+
+def _leader_regions(line: str):
+    """The text inside each `if (lead) { ... }` and `if (!sh_ || lead) { ... }` of a line."""
+    out = []
+    for head in ("if (lead) {", "if (!sh_ || lead) {"):
+        start = 0
+        while (i := line.find(head, start)) >= 0:
+            depth, j = 0, i + len(head) - 1
+            while j < len(line):
+                depth += {"{": 1, "}": -1}.get(line[j], 0)
+                if depth == 0:
+                    break
+                j += 1
+            out.append(line[i + len(head):j])
+            start = j
+    return out
+
+
+def test_warp_form_keeps_collectives_out_of_leader_code(tmp_path, monkeypatch):
+    """In the warp-level form only the leader runs helper calls and shared stores; a
+    collective over the warp's lanes (wmask or the full mask) inside that code would wait
+    for lanes that never come.  Collectives over __activemask() are fine there."""
+    import re
+
+    import numpy as np
+
+    from tests.test_simt_verifier import RANDOM_SPECS, random_handler
+    from workloads import gen
+
+    monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path))
+    cases = [(assemble(EVERY_EFFECT).prog(), EVERY_EFFECT_SPECS, 32, WARP_UNI),
+             (*P.warp_heat(), gen.WARP_UNIFORM)]
+    rng = np.random.default_rng(5)
+    while len(cases) < 6:
+        uniform = np.repeat(rng.random(4) < 0.5, 8)
+        prog = assemble(random_handler(rng)).prog()
+        if gx.verify_simt(prog, RANDOM_SPECS, 32, uniform)[0] == 0:
+            cases.append((prog, RANDOM_SPECS, 32, uniform))
+    warp_wide = re.compile(r"(__shfl_sync|__ballot_sync|__reduce_\w+_sync|group_reduce<[^>]*>)\(\s*(wmask|0x[fF]+u)")
+    for prog, specs, cs, uniform in cases:
+        _check_warp(prog, specs, cs, uniform)
+    sources = list(tmp_path.glob("*.cu"))
+    assert len(sources) >= len(cases) - 1  # identical programs share a source
+    leader_lines = 0
+    for f in sources:
+        for line in f.read_text().splitlines():
+            for region in _leader_regions(line):
+                leader_lines += 1
+                assert not warp_wide.search(region), (f.name, line)
+    assert leader_lines > 20
