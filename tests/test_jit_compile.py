@@ -288,3 +288,20 @@ def test_warp_form_keeps_collectives_out_of_leader_code(tmp_path, monkeypatch):
                 leader_lines += 1
                 assert not warp_wide.search(region), (f.name, line)
     assert leader_lines > 20
+
+
+def test_per_lane_form_has_no_collectives_of_its_own(tmp_path, monkeypatch):
+    """Per-lane generated code runs after data-dependent branches, so a collective in it
+    could wait for lanes on another path.  It has none: warp cooperation happens inside the
+    device helpers, under the mask of the lanes that called them (__activemask())."""
+    monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path))
+    progs = [P.counting(), P.page_heat(), P.latency()] + [P.batch_programs()[p] for p in (0, 9, 33, 63)]
+    for prog, specs, cs in progs:
+        _check(prog, specs, cs)
+    _check(assemble(MANY).prog(), MANY_SPECS, 32)
+    sources = list(tmp_path.glob("*.cu"))
+    assert len(sources) == len(progs) + 1
+    for f in sources:
+        body = f.read_text().split("} // namespace gx")[0]  # the program bodies, before the entry points
+        assert "_sync(" not in body, f.name
+        assert "__activemask()" in body or "agg_update" not in body, f.name
