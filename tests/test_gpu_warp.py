@@ -6,6 +6,10 @@ cover warp_heat over warp-context records with planted bad warps, misaligned lan
 ragged last warp; random SIMT handlers accepted in deterministic mode; one warp of the
 program with every shared effect; several launch shapes and combining widths; and the
 refusals (no interpreter form; a batch that would interpret it).
+
+Before the first run: the generated form puts leader-only code with loops before a
+__shfl_sync, the shape suspected in the one hang this engine's specialisation caused.
+Settle that by reading first, then run the smallest case alone under a short time limit.
 """
 import numpy as np
 import pytest
