@@ -550,7 +550,8 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     break;
                 default: log = "jit: unknown helper"; return GX_EINVAL;
                 }
-                if (p.warp) o << " } r0 = __shfl_sync(wmask, r0, leader);";
+                /* the lanes wait for the leader's work and see its memory effects, then take its result */
+                if (p.warp) o << " } __syncwarp(wmask); r0 = __shfl_sync(wmask, r0, leader);";
                 break;
             }
             const char *c = cond_op(code);
@@ -623,7 +624,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             }
             auto close = [&]() {
                 if (!p.warp || ii.kind == MK_STACK) return;
-                o << " }";
+                o << " } __syncwarp(wmask);"; /* later loads of any lane see the leader's write */
                 if (!bcast.empty()) o << " if (sh_) " << bcast << " = __shfl_sync(wmask, " << bcast << ", leader);";
                 o << " }";
             };

@@ -276,7 +276,8 @@ def test_warp_form_keeps_collectives_out_of_leader_code(tmp_path, monkeypatch):
         prog = assemble(random_handler(rng)).prog()
         if gx.verify_simt(prog, RANDOM_SPECS, 32, uniform)[0] == 0:
             cases.append((prog, RANDOM_SPECS, 32, uniform))
-    warp_wide = re.compile(r"(__shfl_sync|__ballot_sync|__reduce_\w+_sync|group_reduce<[^>]*>)\(\s*(wmask|0x[fF]+u)")
+    warp_wide = re.compile(r"(__shfl_sync|__ballot_sync|__syncwarp|__reduce_\w+_sync|group_reduce<[^>]*>)\(\s*"
+                           r"(wmask|0x[fF]+u)")
     for prog, specs, cs, uniform in cases:
         _check_warp(prog, specs, cs, uniform)
     sources = list(tmp_path.glob("*.cu"))
@@ -288,6 +289,13 @@ def test_warp_form_keeps_collectives_out_of_leader_code(tmp_path, monkeypatch):
                 leader_lines += 1
                 assert not warp_wide.search(region), (f.name, line)
     assert leader_lines > 20
+    # every leader-only region is followed by a barrier of the warp's lanes before anything else
+    for f in sources:
+        for line in f.read_text().splitlines():
+            for head in ("if (lead) {", "if (!sh_ || lead) {"):
+                if head in line:
+                    tail = line.split(head, 1)[1]
+                    assert "__syncwarp(wmask);" in tail, (f.name, line)
 
 
 def test_per_lane_form_has_no_collectives_of_its_own(tmp_path, monkeypatch):
