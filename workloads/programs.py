@@ -14,6 +14,8 @@ tests and the engine tests; they carry no execution semantics.
 * warp_heat  -- page_heat's policy as a warp-level handler (Sec. 4.4.1-4.4.2) over
                 warp-context records: lane addresses reach the maps only through warp
                 reductions; for SIMT-aware verification and the oracle's warp run.
+* sched_policy -- `should_try_steal` block-scheduling policies (FixedWork, Greedy,
+                LatencyBudget) over the block context a persistent worker sees.
 * random_program -- seed-generated verifier-friendly programs for the multi-program batch.
 """
 from __future__ import annotations
@@ -306,6 +308,58 @@ def warp_heat(max_entries: int = 1 << 16) -> Tuple[np.ndarray, List[MapSpec], in
     a.mov("r0", 0)
     a.exit()
     return a.prog(), [hash_spec(max_entries, 8, 16, insert_only=True), array_spec(PAGE_HEAT_TALLY, 16)], 32
+
+
+# --------------------------------------------------------------------------------------
+# Block-scheduling hook context (the `should_try_steal` hook of Sec. 4.3.2): what a worker
+# block of the persistent kernel knows when its own share of work units is done and it may
+# take more from the shared pool.  32 bytes, every field the same for the block's threads.
+SCHED_BLOCK, SCHED_SM, SCHED_DONE, SCHED_LEFT, SCHED_ELAPSED, SCHED_BUDGET = 0, 4, 8, 12, 16, 24
+SCHED_CTX = 32
+SCHED_STATS = 8  # array map: per policy decision kind, {decisions, steals}
+
+
+def _sched_tally(a: Asm) -> None:
+    """stats[SCHED_SM & 7] = {decisions += 1, steals += r0}; r0 kept"""
+    a.mov("r7", "r0")
+    a.ldx(4, "r2", "r6", SCHED_SM)
+    a.alu("and", "r2", 7)
+    a.stx(4, "r10", -4, "r2")
+    a.ld_map("r1", 0)
+    a.mov("r2", "r10")
+    a.add("r2", -4)
+    a.call("map_lookup_elem")
+    a.jeq("r0", 0, "out")
+    a.mov("r1", 1)
+    a.atomic(8, "add", "r0", 0, "r1")
+    a.atomic(8, "add", "r0", 8, "r7")
+    a.label("out")
+    a.mov("r0", "r7")
+    a.exit()
+
+
+def sched_policy(kind: str) -> Tuple[np.ndarray, List[MapSpec], int]:
+    """A `should_try_steal` policy (Sec. 4.3.2, the schedulers of Sec. 6): R0 = 1 to take
+    another unit from the shared pool, 0 to stop.  FixedWork never steals; Greedy steals
+    while the pool has units; LatencyBudget steals while the pool has units and the block's
+    elapsed time is under its budget.  Each also counts its decisions and steals per SM
+    group (array map 0, SCHED_STATS entries of {u64, u64})."""
+    a = Asm()
+    a.mov("r6", "r1")
+    a.mov("r0", 0)
+    if kind != "fixed":
+        a.ldx(4, "r2", "r6", SCHED_LEFT)
+        a.jeq("r2", 0, "decide")
+        if kind == "latency_budget":
+            a.ldx(8, "r3", "r6", SCHED_ELAPSED)
+            a.ldx(8, "r4", "r6", SCHED_BUDGET)
+            a.jge("r3", "r4", "decide")
+        elif kind != "greedy":
+            raise ValueError(kind)
+        a.mov("r0", 1)
+    a.label("decide")
+    _sched_tally(a)
+    return a.prog(), [array_spec(SCHED_STATS, 16)], SCHED_CTX
 
 
 # --------------------------------------------------------------------------------------
