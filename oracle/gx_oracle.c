@@ -10,6 +10,9 @@
  *   for every event i in index order, run the program once on a fresh register file
  *   with R1 = pointer to that event's ctx_size-byte record and R10 = the top of a fresh
  *   512-byte stack; map and ring-buffer state carries over from event to event.
+ * Two further forms, defined where they are written out below: the warp run (or_run_warps,
+ * the warp-level execution of Sec. 4.4.1 / 4.4.2) and the strict-alignment run
+ * (or_run_flags with OR_STRICT_ALIGN).
  * The paper runs verified eBPF handlers on device events (Sec. 4.3, Sec. 4.4, Sec. 5.3)
  * and names the instruction set only as a restricted eBPF subset, so the instruction
  * semantics follow the standard eBPF ISA (RFC 9669):
