@@ -132,3 +132,33 @@ def allgather_merge(dist, local, merge: Callable[[list], object]):
     copies = [None] * dist.get_world_size()
     dist.all_gather_object(copies, local)
     return merge(copies)
+
+
+def merge_snapshots(prog: np.ndarray, specs: Sequence[dict], ctx_size: int, copies: Sequence[Sequence],
+                    init: Optional[Sequence[Optional[np.ndarray]]] = None) -> list:
+    """Merge every map of one program at once.  copies[c][m] is engine c's snapshot of map m:
+    array bytes (max_entries x value_size), a {key: value} dict, or a ring's (records,
+    dropped).  init[m]: the contents array map m started from (None: zeros).  Raises
+    ValueError when gx_merge_ops refuses the program or a map (its log says why)."""
+    out = []
+    for m, spec in enumerate(specs):
+        parts = [c[m] for c in copies]
+        if spec["type"] == G.MAP_RINGBUF:
+            out.append(merge_ring(parts))
+            continue
+        rc, ops, insert, log = G.merge_ops(prog, specs, ctx_size, m)
+        if rc != 0:
+            raise ValueError(f"map {m} cannot be merged: {log}")
+        if spec["type"] == G.MAP_ARRAY:
+            start = None if init is None or init[m] is None else np.asarray(init[m], dtype=np.uint8)
+            out.append(merge_array(ops, parts, init=start))
+        else:
+            out.append(merge_hash(ops, parts, insert=insert))
+    return out
+
+
+def merge_across_ranks(dist, prog: np.ndarray, specs: Sequence[dict], ctx_size: int, local: Sequence,
+                       init: Optional[Sequence[Optional[np.ndarray]]] = None) -> list:
+    """Every rank passes its own snapshots of the program's maps; every rank gets the merged
+    maps (merge_snapshots over the ranks' snapshots, in rank order)."""
+    return allgather_merge(dist, list(local), lambda copies: merge_snapshots(prog, specs, ctx_size, copies, init))

@@ -46,20 +46,8 @@ def run_parts(prog, specs, cs, ev, cuts, init=None):
 
 
 def merge_parts(prog, specs, cs, parts, init=None):
-    out = []
-    for j, s in enumerate(specs):
-        copies = [p[j] for p in parts]
-        if s["type"] == O.MAP_RINGBUF:
-            out.append(M.merge_ring(copies))
-            continue
-        rc, ops, insert, log = gx.merge_ops(prog, specs, cs, j)
-        assert rc == 0, log
-        if s["type"] == O.MAP_ARRAY:
-            start = None if not init or init[j] is None else np.frombuffer(init[j], np.uint8)
-            out.append(M.merge_array(ops, copies, init=start))
-        else:
-            out.append(M.merge_hash(ops, copies, insert=insert))
-    return out
+    start = None if not init else [None if v is None else np.frombuffer(v, np.uint8) for v in init]
+    return M.merge_snapshots(prog, specs, cs, parts, init=start)
 
 
 def assert_merge_equals_whole(prog, specs, cs, ev, cuts, init=None):
@@ -199,7 +187,7 @@ def _rank_main(rank: int, world: int, port: int, out) -> None:
             n = len(np.ascontiguousarray(ev).view(np.uint8)) // cs
             cuts = [n * r // world for r in range(world + 1)]
             mine = run_parts(prog, specs, cs, ev, cuts[rank:rank + 2])[0]  # this rank's part only
-            merged = M.allgather_merge(dist, mine, lambda parts: merge_parts(prog, specs, cs, parts))
+            merged = M.merge_across_ranks(dist, prog, specs, cs, mine)
             whole = run_parts(prog, specs, cs, ev, [0, n])[0]
             ok.append(all(np.array_equal(w, m) if s["type"] == O.MAP_ARRAY else w == m
                           for s, w, m in zip(specs, whole, merged)))
