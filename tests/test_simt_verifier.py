@@ -330,3 +330,25 @@ def test_warp_heat_budgets_and_their_worst_path():
     lines = ["ldx8 r7 r1 0", "rsh r7 21", "stx8 r10 -8 r7", "ld_map r1 0", "mov r2 r10", "add r2 -8",
              "call map_lookup_elem", "mov r0 0", "exit"]
     rejected(lines, specs, gx.SIMT_V_KEY, 7, uniform=gen.WARP_UNIFORM, ctx_size=32)
+
+
+def test_all_uniform_simt_mode_judges_like_the_per_lane_verifier():
+    """With every ctx byte uniform nothing is lane-varying, so SIMT mode (path counters and
+    the pruning they restrict included) must accept and reject exactly what the per-lane
+    verifier does, for the same reason, over the memory-safety fuzzer's random programs."""
+    from tests.test_verifier_fuzz import CTX, SPECS as FSPECS, Gen
+
+    rng = np.random.default_rng(777)
+    both = 0
+    for _ in range(500):
+        prog = assemble(Gen(rng).program()).prog()
+        rc1, log1 = gx.verify(prog, FSPECS, CTX)
+        rc2, rep, log2 = gx.verify_simt(prog, FSPECS, CTX, np.ones(CTX, bool))
+        # the same verdict for the same reason; exploring in another order may stop elsewhere
+        assert rc1 == rc2 and log1.split(": ", 1)[-1] == log2.split(": ", 1)[-1], (log1, log2)
+        if rc1 == 0:
+            both += 1
+            assert rep.varying_insns == 0 and rep.max_insns > 0
+        else:
+            assert rep.violation == gx.SIMT_V_VERIFY
+    assert both >= 60
