@@ -74,7 +74,7 @@ def lib() -> ctypes.CDLL:
             L.or_run.argtypes = [vp, u32, vp, u32, vp, u64, u32, u64, vp, ctypes.POINTER(u64), u64,
                                  ctypes.POINTER(u64)]
             L.or_run.restype = i32
-            L.or_run_flags.argtypes = L.or_run.argtypes + [u32]
+            L.or_run_flags.argtypes = L.or_run.argtypes + [u32, ctypes.POINTER(u64)]
             L.or_run_flags.restype = i32
             L.or_run_warps.argtypes = [vp, u32, vp, u32, vp, u64, u32, vp, u32, u64, vp, ctypes.POINTER(u64), u64,
                                        ctypes.POINTER(u64), ctypes.POINTER(u32)]
@@ -169,12 +169,14 @@ def parse_records(raw: bytes) -> List[Tuple[int, bytes]]:
 
 
 def run(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_size: int, *, event_idx_base: int = 0,
-        want_r0: bool = False, budget: int = 0, strict_align: bool = False) -> Tuple[Optional[np.ndarray], int]:
+        want_r0: bool = False, budget: int = 0, strict_align: bool = False,
+        most: Optional[list] = None) -> Tuple[Optional[np.ndarray], int]:
     """Run `prog` over `events` (contiguous records of ctx_size bytes).
 
     Returns (R0 per event as int64 or None, total executed instructions); raises
     OracleError on a fault.  strict_align: a load, store or atomic at an address that is
-    not a multiple of its size is a fault (EFAULT) too."""
+    not a multiple of its size is a fault (EFAULT) too.  most (a list, filled in): the most
+    instructions, helper calls and loads / stores / atomics one event executed."""
     prog = np.ascontiguousarray(prog, dtype=np.uint64)
     raw = np.ascontiguousarray(events).view(np.uint8).reshape(-1)
     assert raw.size % ctx_size == 0
@@ -183,9 +185,12 @@ def run(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_size: int
     r0 = np.zeros(n, dtype=np.int64) if want_r0 else None
     count = ctypes.c_uint64(0)
     bad = ctypes.c_uint64(0)
+    top = (ctypes.c_uint64 * 3)()
     rc = lib().or_run_flags(prog.ctypes.data, prog.size, handles, len(maps), raw.ctypes.data, n, ctx_size,
                             event_idx_base, None if r0 is None else r0.ctypes.data, ctypes.byref(count), budget,
-                            ctypes.byref(bad), 1 if strict_align else 0)
+                            ctypes.byref(bad), 1 if strict_align else 0, top)
+    if most is not None:
+        most[:] = [int(x) for x in top]
     if rc != 0:
         raise OracleError(rc, int(bad.value))
     return r0, int(count.value)

@@ -471,6 +471,7 @@ typedef struct {
     regions *g;
     region granted; /* the region the last helper call granted (size 0: none) */
     int strict_align;
+    uint64_t helpers, mem; /* this event's helper calls and loads / stores / atomics */
 } hctx;
 
 static or_map *map_arg(const hctx *h, uint64_t v) {
@@ -749,6 +750,7 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
             }
             if (code == 0x80 && cls == 5) { /* CALL */
                 if (src != 0) return OR_EINVAL;
+                h->helpers++;
                 rc = helper(h, imm, R);
                 break;
             }
@@ -767,10 +769,12 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
             next = pc + 2;
             break;
         case 1: /* LDX */
+            h->mem++;
             rc = ins_ldx(R, &g, op, dst, src, off);
             break;
         case 2: /* ST */
         case 3: /* STX */
+            h->mem++;
             rc = ins_store(R, &g, op, dst, src, off, imm);
             break;
         default: return OR_EINVAL;
@@ -788,11 +792,13 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
  * or_run_flags: OR_STRICT_ALIGN also stops with OR_EFAULT at a load, store or atomic (the
  * max / min helpers included) whose address is not a multiple of its size, the engine's
  * reading that device accesses are naturally aligned; or_run leaves alignment free.
+ * most (nullable): the most instructions, helper calls and loads / stores / atomics that
+ * one event executed.
  */
 #define OR_STRICT_ALIGN 1u
 int or_run_flags(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
                  uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out,
-                 uint64_t *insn_count, uint64_t budget, uint64_t *bad_event, uint32_t flags) {
+                 uint64_t *insn_count, uint64_t budget, uint64_t *bad_event, uint32_t flags, uint64_t *most) {
     hctx h;
     memset(&h, 0, sizeof h);
     h.strict_align = (flags & OR_STRICT_ALIGN) != 0;
@@ -800,11 +806,18 @@ int or_run_flags(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_
     h.n_maps = n_maps;
     uint64_t count = 0;
     if (budget == 0) budget = 1ULL << 20;
+    if (most) most[0] = most[1] = most[2] = 0;
     for (uint64_t i = 0; i < n_events; i++) {
-        uint64_t ret = 0;
+        uint64_t ret = 0, before = count;
         h.event_idx = event_idx_base + i;
+        h.helpers = h.mem = 0;
         int rc = run_one(insns, n_insns, &h, (uint8_t *)(uintptr_t)(events + i * (uint64_t)ctx_size), ctx_size,
                          budget, &ret, &count);
+        if (most && rc == OR_OK) {
+            if (count - before > most[0]) most[0] = count - before;
+            if (h.helpers > most[1]) most[1] = h.helpers;
+            if (h.mem > most[2]) most[2] = h.mem;
+        }
         if (rc != OR_OK) {
             if (bad_event) *bad_event = i;
             if (insn_count) *insn_count = count;
@@ -820,7 +833,7 @@ int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_ma
            uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out, uint64_t *insn_count,
            uint64_t budget, uint64_t *bad_event) {
     return or_run_flags(insns, n_insns, maps, n_maps, events, n_events, ctx_size, event_idx_base, r0_out, insn_count,
-                        budget, bad_event, 0);
+                        budget, bad_event, 0, NULL);
 }
 
 /* ------------------------------------------------------------------ one warp, in lockstep */

@@ -115,3 +115,19 @@ def test_strict_alignment_of_the_max_helper():
     with pytest.raises(O.OracleError) as e:
         O.run(assemble([x.format(4) for x in look]).prog(), O.maps_from_specs(specs), ev, 16, strict_align=True)
     assert e.value.rc == O.EFAULT
+
+
+def test_most_counts_per_event():
+    """`most`: the largest instruction, helper-call and memory-operation counts of one event.
+    Event 0 (word 0 = 0) takes the short path: mov, ldx, jeq, mov, exit = 5 instructions,
+    1 memory operation.  Event 1 takes the long one: mov, ldx, jeq, st, ldx, ld_map (one
+    instruction), mov, add, call, mov, exit = 11 instructions, 3 memory operations, 1 call."""
+    lines = ["mov r6 r1", "ldx8 r2 r6 0", "jeq r2 0 out", "st4 r10 -4 0", "ldx4 r3 r10 -4", "ld_map r1 0",
+             "mov r2 r10", "add r2 -4", "call map_lookup_elem", "out:", "mov r0 0", "exit"]
+    specs = [dict(type=2, key_size=4, value_size=8, max_entries=1)]
+    prog = assemble(lines).prog()
+    for ev, want in ((np.array([[0, 0]], np.uint64), [5, 0, 1]),
+                     (np.array([[0, 0], [1, 0], [0, 0]], np.uint64), [11, 1, 3])):
+        most = []
+        O.run(prog, O.maps_from_specs(specs), ev, 16, most=most)
+        assert most == want

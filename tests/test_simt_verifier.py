@@ -335,7 +335,9 @@ def test_warp_heat_budgets_and_their_worst_path():
 def test_all_uniform_simt_mode_judges_like_the_per_lane_verifier():
     """With every ctx byte uniform nothing is lane-varying, so SIMT mode (path counters and
     the pruning they restrict included) must accept and reject exactly what the per-lane
-    verifier does, for the same reason, over the memory-safety fuzzer's random programs."""
+    verifier does, for the same reason, over the memory-safety fuzzer's random programs; and
+    the instruction, helper-call and memory-operation maxima it reports bound what any event
+    of an accepted program executes on the oracle."""
     from tests.test_verifier_fuzz import CTX, SPECS as FSPECS, Gen
 
     rng = np.random.default_rng(777)
@@ -349,6 +351,13 @@ def test_all_uniform_simt_mode_judges_like_the_per_lane_verifier():
         if rc1 == 0:
             both += 1
             assert rep.varying_insns == 0 and rep.max_insns > 0
+            # the reported path maxima bound what any event executes
+            ev = rng.integers(0, 2**64 - 1, size=(32, CTX // 8), dtype=np.uint64, endpoint=True)
+            ev[::3] &= np.uint64(0xFF)
+            most = []
+            O.run(prog, O.maps_from_specs(FSPECS), ev, CTX, most=most)
+            assert most[0] <= rep.max_insns and most[1] <= rep.max_helper_calls and most[2] <= rep.max_mem_ops, \
+                (most, rep.max_insns, rep.max_helper_calls, rep.max_mem_ops)
         else:
             assert rep.violation == gx.SIMT_V_VERIFY
     assert both >= 60
