@@ -8,7 +8,7 @@
  *   - device program type with a compact read-only context (Sec. 4.3, Sec. 4.3.1);
  *   - verification before execution: typed registers, bounded loops, memory safety,
  *     per-hook resource budgets (Sec. 4.4, Sec. 4.4.1, Sec. 5.3);
- *   - warp-level aggregated map updates (Sec. 4.4.2, Sec. 5.3 "Hierarchical Maps");
+ *   - warp-level aggregated map updates (Sec. 4.4.2, and the hierarchical maps of Sec. 5.3);
  *   - maps as the shared key-value state, snapshotted at kernel completion (Sec. 4.4.3);
  *   - persistent workers claiming logical work units (Sec. 4.3.2, Sec. 5.3).
  * Instruction semantics follow the standard eBPF ISA (RFC 9669); map helpers use the

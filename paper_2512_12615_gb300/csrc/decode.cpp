@@ -1,8 +1,8 @@
 /*
  * Decoder: verified eBPF -> device micro-ops (layout in gx_layout.h).
  *
- * The paper specialises device handlers when it compiles them (Sec. 4.4.2, Sec. 5.3:
- * "specialization and inlining"); the engine's counterpart is done once at load time:
+ * The paper specialises device handlers and inlines their helpers when it compiles them
+ * (Sec. 4.4.2, Sec. 5.3); the engine's counterpart is done once at load time:
  * every instruction becomes one to four micro-ops whose handler already names the
  * eBPF register, the memory region (ctx / stack / global) and, for ctx and stack
  * accesses, the absolute offset proven by the verifier.  Jump offsets become absolute
