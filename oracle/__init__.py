@@ -32,6 +32,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 MAP_HASH, MAP_ARRAY, MAP_RINGBUF = 1, 2, 27
 ENOENT, E2BIG, EAGAIN, ENOMEM, EFAULT, EEXIST, EINVAL, EBUDGET = -2, -7, -11, -12, -14, -17, -22, -1002
 EDIVERGE = -1003  # run_warps: the lanes of a warp disagree where they must agree
+EDEFER = -1004  # run with defer_maps: a deferred map's values were used other than by a combinable update
 
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
@@ -74,7 +75,7 @@ def lib() -> ctypes.CDLL:
             L.or_run.argtypes = [vp, u32, vp, u32, vp, u64, u32, u64, vp, ctypes.POINTER(u64), u64,
                                  ctypes.POINTER(u64)]
             L.or_run.restype = i32
-            L.or_run_flags.argtypes = L.or_run.argtypes + [u32, ctypes.POINTER(u64)]
+            L.or_run_flags.argtypes = L.or_run.argtypes + [u32, ctypes.POINTER(u64), u32]
             L.or_run_flags.restype = i32
             L.or_run_warps.argtypes = [vp, u32, vp, u32, vp, u64, u32, vp, u32, u64, vp, ctypes.POINTER(u64), u64,
                                        ctypes.POINTER(u64), ctypes.POINTER(u32)]
@@ -170,13 +171,15 @@ def parse_records(raw: bytes) -> List[Tuple[int, bytes]]:
 
 def run(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_size: int, *, event_idx_base: int = 0,
         want_r0: bool = False, budget: int = 0, strict_align: bool = False,
-        most: Optional[list] = None) -> Tuple[Optional[np.ndarray], int]:
+        most: Optional[list] = None, defer_maps: int = 0) -> Tuple[Optional[np.ndarray], int]:
     """Run `prog` over `events` (contiguous records of ctx_size bytes).
 
     Returns (R0 per event as int64 or None, total executed instructions); raises
     OracleError on a fault.  strict_align: a load, store or atomic at an address that is
     not a multiple of its size is a fault (EFAULT) too.  most (a list, filled in): the most
-    instructions, helper calls and loads / stores / atomics one event executed."""
+    instructions, helper calls and loads / stores / atomics one event executed.  defer_maps:
+    bit m defers map m's non-fetching commutative updates to after the last event; any
+    other use of its values raises EDEFER (the oracle's model of block-private combining)."""
     prog = np.ascontiguousarray(prog, dtype=np.uint64)
     raw = np.ascontiguousarray(events).view(np.uint8).reshape(-1)
     assert raw.size % ctx_size == 0
@@ -188,7 +191,7 @@ def run(prog: np.ndarray, maps: Sequence[Map], events: np.ndarray, ctx_size: int
     top = (ctypes.c_uint64 * 3)()
     rc = lib().or_run_flags(prog.ctypes.data, prog.size, handles, len(maps), raw.ctypes.data, n, ctx_size,
                             event_idx_base, None if r0 is None else r0.ctypes.data, ctypes.byref(count), budget,
-                            ctypes.byref(bad), 1 if strict_align else 0, top)
+                            ctypes.byref(bad), 1 if strict_align else 0, top, defer_maps)
     if most is not None:
         most[:] = [int(x) for x in top]
     if rc != 0:

@@ -294,6 +294,78 @@ void or_ringbuf_reset(or_map *m) {
     m->dropped = 0;
 }
 
+/* ------------------------------------------------------------------ deferred updates */
+/*
+ * Deferral (or_run_flags with a defer mask): the engine's block-private combining taken to
+ * its extreme.  Non-fetching ADD / OR / AND / XOR atomics and the max / min helpers into
+ * the values of a deferred map are logged instead of applied, and the log is applied in
+ * order after the last event.  Any other access to a deferred map's values stops the run
+ * with OR_EDEFER: a load, a plain store, a fetch or exchange, a helper reading them, an
+ * update that may overwrite, a delete.  For a map the verifier calls combinable none of
+ * these happens, and then the deferred run's results equal the plain run's.
+ */
+#define OR_EDEFER (-1004)
+#define DEFER_MAX 1 /* op codes besides the BPF_ATOMIC ones (0x00, 0x40, 0x50, 0xA0) */
+#define DEFER_MIN 2
+
+typedef struct {
+    uint8_t *p;
+    int size, op;
+    uint64_t v;
+} dop;
+
+typedef struct {
+    uint32_t mask;
+    or_map **maps;
+    uint32_t n_maps;
+    dop *log;
+    size_t n, cap;
+} defer_t;
+
+static int overlaps_values(const or_map *m, uint64_t a, uint64_t size) {
+    if (m->type == MAP_ARRAY) {
+        uint64_t b = (uint64_t)(uintptr_t)m->values;
+        return a < b + (uint64_t)m->max_entries * m->value_size && a + size > b;
+    }
+    if (m->type == MAP_HASH)
+        for (const hnode *n = m->all; n; n = n->all_next) {
+            uint64_t b = (uint64_t)(uintptr_t)n->value;
+            if (a < b + m->value_size && a + size > b) return 1;
+        }
+    return 0;
+}
+
+/* [a, a + size) overlaps the values of a deferred map */
+static int deferred(const defer_t *d, uint64_t a, uint64_t size) {
+    if (!d) return 0;
+    for (uint32_t i = 0; i < d->n_maps; i++)
+        if (((d->mask >> i) & 1) && overlaps_values(d->maps[i], a, size)) return 1;
+    return 0;
+}
+
+static int deferred_map(const defer_t *d, const or_map *m) {
+    if (!d) return 0;
+    for (uint32_t i = 0; i < d->n_maps; i++)
+        if (d->maps[i] == m) return (d->mask >> i) & 1;
+    return 0;
+}
+
+static int defer_log(defer_t *d, uint8_t *p, int size, int op, uint64_t v) {
+    if (d->n == d->cap) {
+        size_t cap = d->cap ? 2 * d->cap : 1024;
+        dop *log = (dop *)realloc(d->log, cap * sizeof(dop));
+        if (!log) return OR_ENOMEM;
+        d->log = log;
+        d->cap = cap;
+    }
+    d->log[d->n].p = p;
+    d->log[d->n].size = size;
+    d->log[d->n].op = op;
+    d->log[d->n].v = v;
+    d->n++;
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------ interpreter */
 typedef struct {
     uint8_t *base;
@@ -305,6 +377,7 @@ typedef struct {
     region r[MAX_REGIONS];
     int n;
     int strict_align; /* or_run_flags OR_STRICT_ALIGN: instruction accesses must be naturally aligned */
+    defer_t *defer;   /* or_run_flags with a defer mask: the deferral state */
 } regions;
 
 static void grant(regions *g, uint8_t *base, uint64_t size, int writable) {
@@ -472,6 +545,7 @@ typedef struct {
     region granted; /* the region the last helper call granted (size 0: none) */
     int strict_align;
     uint64_t helpers, mem; /* this event's helper calls and loads / stores / atomics */
+    defer_t *defer;
 } hctx;
 
 static or_map *map_arg(const hctx *h, uint64_t v) {
@@ -517,6 +591,7 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
     case 1: { /* map_lookup_elem(map, key) */
         or_map *m = map_arg(h, R[1]);
         if (!m || m->type == MAP_RINGBUF) return OR_EFAULT;
+        if (deferred(h->defer, R[2], m->key_size)) return OR_EDEFER;
         uint8_t *k = check(g, R[2], m->key_size, 0);
         if (!k) return OR_EFAULT;
         uint8_t *v = map_lookup(m, k);
@@ -530,6 +605,9 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
     case 2: { /* map_update_elem(map, key, value, flags) */
         or_map *m = map_arg(h, R[1]);
         if (!m || m->type == MAP_RINGBUF) return OR_EFAULT;
+        if (deferred(h->defer, R[2], m->key_size) || deferred(h->defer, R[3], m->value_size) ||
+            (deferred_map(h->defer, m) && R[4] != 1))
+            return OR_EDEFER; /* a deferred map may only gain keys (NOEXIST inserts) */
         uint8_t *k = check(g, R[2], m->key_size, 0);
         uint8_t *v = check(g, R[3], m->value_size, 0);
         if (!k || !v) return OR_EFAULT;
@@ -543,6 +621,7 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
     case 3: { /* map_delete_elem(map, key) */
         or_map *m = map_arg(h, R[1]);
         if (!m || m->type == MAP_RINGBUF) return OR_EFAULT;
+        if (deferred_map(h->defer, m) || deferred(h->defer, R[2], m->key_size)) return OR_EDEFER;
         uint8_t *k = check(g, R[2], m->key_size, 0);
         if (!k) return OR_EFAULT;
         r0 = (uint64_t)(int64_t)map_delete(m, k);
@@ -555,6 +634,7 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
             r0 = (uint64_t)(int64_t)OR_EINVAL;
             break;
         }
+        if (deferred(h->defer, R[2], R[3])) return OR_EDEFER;
         uint8_t *src = check(g, R[2], R[3], 0);
         if (!src && R[3]) return OR_EFAULT;
         uint8_t tmp[4096];
@@ -589,6 +669,12 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
     case 0x10001: { /* atomic_min_u64(ptr, v) */
         uint8_t *p = check(g, R[1], 8, 1);
         if (!p || (g->strict_align && R[1] % 8)) return OR_EFAULT;
+        if (deferred(h->defer, R[1], 8)) {
+            int rc = defer_log(h->defer, p, 8, id == 0x10000 ? DEFER_MAX : DEFER_MIN, R[2]);
+            if (rc != OR_OK) return rc;
+            r0 = 0;
+            break;
+        }
         uint64_t cur = load_le(p, 8);
         if (id == 0x10000 ? R[2] > cur : R[2] < cur) store_le(p, 8, R[2]);
         r0 = 0;
@@ -656,6 +742,7 @@ static int ins_ldx(uint64_t *R, const regions *g, uint8_t op, int dst, int src, 
     int sz = size_of(op);
     if (dst == 10 || (mode != 0x60 && mode != 0x80) || (mode == 0x80 && sz == 8)) return OR_EINVAL;
     uint64_t a = R[src] + (uint64_t)(int64_t)off;
+    if (deferred(g->defer, a, (uint64_t)sz)) return OR_EDEFER;
     uint8_t *p = check(g, a, (uint64_t)sz, 0);
     if (!p || (g->strict_align && a % (uint64_t)sz)) return OR_EFAULT;
     uint64_t v = load_le(p, sz);
@@ -672,6 +759,15 @@ static int ins_store(uint64_t *R, const regions *g, uint8_t op, int dst, int src
     int sz = size_of(op);
     uint64_t a = store_addr(R, dst, off);
     if (g->strict_align && a % (uint64_t)sz) return OR_EFAULT;
+    if (deferred(g->defer, a, (uint64_t)sz)) { /* only a non-fetching ADD / OR / AND / XOR is deferred */
+        const int base = imm & ~1;
+        if (mode != 0xC0 || cls != 3 || (imm & 1) || (sz != 4 && sz != 8) ||
+            !(base == 0x00 || base == 0x40 || base == 0x50 || base == 0xA0))
+            return OR_EDEFER;
+        uint8_t *p = check(g, a, (uint64_t)sz, 1);
+        if (!p) return OR_EFAULT;
+        return defer_log(g->defer, p, sz, base, R[src] & (sz == 4 ? 0xFFFFFFFFULL : ~0ULL));
+    }
     if (mode == 0x60) {
         uint8_t *p = check(g, a, (uint64_t)sz, 1);
         if (!p) return OR_EFAULT;
@@ -717,6 +813,7 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
     memset(stack, 0, sizeof stack);
     g.n = 0;
     g.strict_align = h->strict_align;
+    g.defer = h->defer;
     grant(&g, ctx, ctx_size, 0);
     grant(&g, stack, STACK_BYTES, 1);
     h->g = &g;
@@ -793,47 +890,73 @@ static int run_one(const uint64_t *insns, uint32_t n, hctx *h, uint8_t *ctx, uin
  * max / min helpers included) whose address is not a multiple of its size, the engine's
  * reading that device accesses are naturally aligned; or_run leaves alignment free.
  * most (nullable): the most instructions, helper calls and loads / stores / atomics that
- * one event executed.
+ * one event executed.  defer_mask: bit m defers map m's updates (see "deferred updates").
  */
 #define OR_STRICT_ALIGN 1u
+/* the deferred updates, in the order they were made */
+static void defer_apply(const defer_t *d) {
+    for (size_t i = 0; i < d->n; i++) {
+        const dop *o = &d->log[i];
+        uint64_t mask = o->size == 4 ? 0xFFFFFFFFULL : ~0ULL, old = load_le(o->p, o->size), r = old;
+        switch (o->op) {
+        case 0x00: r = (old + o->v) & mask; break;
+        case 0x40: r = old | o->v; break;
+        case 0x50: r = old & o->v; break;
+        case 0xA0: r = old ^ o->v; break;
+        case DEFER_MAX: r = o->v > old ? o->v : old; break;
+        case DEFER_MIN: r = o->v < old ? o->v : old; break;
+        }
+        store_le(o->p, o->size, r);
+    }
+}
+
 int or_run_flags(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
                  uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out,
-                 uint64_t *insn_count, uint64_t budget, uint64_t *bad_event, uint32_t flags, uint64_t *most) {
+                 uint64_t *insn_count, uint64_t budget, uint64_t *bad_event, uint32_t flags, uint64_t *most,
+                 uint32_t defer_mask) {
     hctx h;
     memset(&h, 0, sizeof h);
     h.strict_align = (flags & OR_STRICT_ALIGN) != 0;
+    defer_t d;
+    memset(&d, 0, sizeof d);
+    d.mask = defer_mask;
+    d.maps = maps;
+    d.n_maps = n_maps;
+    if (defer_mask) h.defer = &d;
+    int rc = OR_OK;
     h.maps = maps;
     h.n_maps = n_maps;
     uint64_t count = 0;
     if (budget == 0) budget = 1ULL << 20;
     if (most) most[0] = most[1] = most[2] = 0;
-    for (uint64_t i = 0; i < n_events; i++) {
+    for (uint64_t i = 0; i < n_events && rc == OR_OK; i++) {
         uint64_t ret = 0, before = count;
         h.event_idx = event_idx_base + i;
         h.helpers = h.mem = 0;
-        int rc = run_one(insns, n_insns, &h, (uint8_t *)(uintptr_t)(events + i * (uint64_t)ctx_size), ctx_size,
-                         budget, &ret, &count);
-        if (most && rc == OR_OK) {
+        rc = run_one(insns, n_insns, &h, (uint8_t *)(uintptr_t)(events + i * (uint64_t)ctx_size), ctx_size,
+                     budget, &ret, &count);
+        if (rc != OR_OK) {
+            if (bad_event) *bad_event = i;
+            break;
+        }
+        if (most) {
             if (count - before > most[0]) most[0] = count - before;
             if (h.helpers > most[1]) most[1] = h.helpers;
             if (h.mem > most[2]) most[2] = h.mem;
         }
-        if (rc != OR_OK) {
-            if (bad_event) *bad_event = i;
-            if (insn_count) *insn_count = count;
-            return rc;
-        }
         if (r0_out) r0_out[i] = (int64_t)ret;
     }
+    if (rc == OR_OK) defer_apply(&d);
+    free(d.log);
     if (insn_count) *insn_count = count;
-    return OR_OK;
+    return rc;
 }
 
 int or_run(const uint64_t *insns, uint32_t n_insns, or_map **maps, uint32_t n_maps, const uint8_t *events,
            uint64_t n_events, uint32_t ctx_size, uint64_t event_idx_base, int64_t *r0_out, uint64_t *insn_count,
            uint64_t budget, uint64_t *bad_event) {
     return or_run_flags(insns, n_insns, maps, n_maps, events, n_events, ctx_size, event_idx_base, r0_out, insn_count,
-                        budget, bad_event, 0, NULL);
+                        budget, bad_event, 0, NULL, 0);
 }
 
 /* ------------------------------------------------------------------ one warp, in lockstep */
@@ -1020,6 +1143,7 @@ static int run_warp(const uint64_t *insns, uint32_t n, hctx *h, lane *L, uint32_
         memset(L[i].stack, 0, sizeof L[i].stack);
         L[i].g.n = 0;
         L[i].g.strict_align = h->strict_align;
+        L[i].g.defer = NULL;
         grant(&L[i].g, L[i].ctx, ctx_size, 0);
         grant(&L[i].g, L[i].stack, STACK_BYTES, 1);
         L[i].R[1] = (uint64_t)(uintptr_t)L[i].ctx;
