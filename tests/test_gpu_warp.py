@@ -9,7 +9,8 @@ refusals (no interpreter form; a batch that would interpret it).
 
 Before the first run: the generated form puts leader-only code with loops before a
 __shfl_sync, the shape suspected in the one hang this engine's specialisation caused.
-Settle that by reading first, then run the smallest case alone under a short time limit.
+Settle that by reading first, then run the smallest cases alone under a short time limit
+(`-m gpu_pending -k first_run`, which run one warp before anything larger).
 """
 import numpy as np
 import pytest
@@ -49,6 +50,24 @@ def run_warp_both(ctx, prog, specs, cs, ev, uniform, launch=None):
     assert np.array_equal(ret.cpu().numpy(), r0)
     assert_same(snapshot_gpu(gm), snapshot_oracle(om))
     p.destroy()
+
+
+def test_first_run_reduction_only(ctx):
+    """The smallest case, to run first: one warp, a warp reduction, no leader block."""
+    ev = np.zeros((32, 2), dtype=np.uint64)
+    ev[:, 1] = np.arange(32, dtype=np.uint64) * np.uint64(3)
+    prog = assemble(["ldx8 r1 r1 8", "call warp_sum_u64", "exit"]).prog()
+    run_warp_both(ctx, prog, [], 16, ev, [True] * 8 + [False] * 8, launch=(64, 1))
+
+
+def test_first_run_one_leader_block(ctx):
+    """Next: one leader block (a lookup), then the barrier and the broadcast."""
+    ev = np.zeros((32, 2), dtype=np.uint64)
+    ev[:, 1] = np.arange(32, dtype=np.uint64)
+    lines = ["ldx8 r7 r1 0", "stx4 r10 -4 r7", "ld_map r1 0", "mov r2 r10", "add r2 -4", "call map_lookup_elem",
+             "mov r6 0", "jeq r0 0 out", "mov r6 1", "out:", "mov r0 r6", "exit"]
+    specs = [dict(type=2, key_size=4, value_size=8, max_entries=4)]
+    run_warp_both(ctx, assemble(lines).prog(), specs, 16, ev, [True] * 8 + [False] * 8, launch=(64, 1))
 
 
 @pytest.mark.parametrize("launch", [None, (64, 1), (256, 8, 255), (256, 4, 0), (128, 2, 4)])
