@@ -107,6 +107,30 @@ extern "C" {
 #define GX_MAX_KEY 64
 #define GX_MAX_VALUE 4096
 
+/*
+ * Scheduling programs (gx_batch_set_sched; the `should_try_steal` hook over a block
+ * context, Sec. 4.3.2).  The context is GX_SCHED_CTX bytes, little-endian, every field
+ * warp-uniform: the block index, its SM, the chunks it has run, the chunks left in the
+ * share it would take from, ns since the block started, and the batch's budget.
+ */
+#define GX_SCHED_CTX 32
+#define GX_SCHED_OFF_BLOCK 0    /* u32 */
+#define GX_SCHED_OFF_SM 4       /* u32 */
+#define GX_SCHED_OFF_DONE 8     /* u32 */
+#define GX_SCHED_OFF_LEFT 12    /* u32 */
+#define GX_SCHED_OFF_ELAPSED 16 /* u64 */
+#define GX_SCHED_OFF_BUDGET 24  /* u64 */
+/* the hook budget a scheduling program is verified against unless the caller names one */
+#define GX_SCHED_MAX_INSNS 64
+#define GX_SCHED_MAX_HELPERS 2
+#define GX_SCHED_MAX_MEM 16
+/* per-block counters of a batch run with a scheduling program (gx_batch_sched_tally) */
+#define GX_STEAL_OWNED 0   /* chunks of the block's own share it ran */
+#define GX_STEAL_STOLEN 1  /* chunks of other shares it ran */
+#define GX_STEAL_ASKED 2   /* times it ran the scheduling program */
+#define GX_STEAL_GRANTED 3 /* times the program answered R0 != 0 */
+#define GX_STEAL_WORDS 4
+
 #ifndef __CUDACC_RTC__ /* device code sees the constants above only */
 typedef struct gx_ctx gx_ctx;
 typedef struct gx_map gx_map;
@@ -328,6 +352,17 @@ int gx_verify_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *m
 int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
                       const gx_prog_opts *opts, const gx_simt_spec *simt, char *log, size_t log_len);
 /*
+ * Host only: compile, without loading it, the persistent kernel of a batch whose one
+ * program (insns, maps, opts) runs under the scheduling program (hook, hook_maps,
+ * hook_opts) as gx_batch_set_sched describes.  Both must verify; the hook must pass the
+ * SIMT check within `limits` (nullable: the GX_SCHED_MAX_* budget) and have ctx_size
+ * GX_SCHED_CTX.  0, GX_E_VERIFY, GX_EINVAL, GX_E_NODEV or GX_E_CUDA; `log` explains.
+ */
+int gx_jit_check_sched(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
+                       const gx_prog_opts *opts, const uint64_t *hook, uint32_t n_hook, const gx_map_spec *hook_maps,
+                       uint32_t n_hook_maps, const gx_prog_opts *hook_opts, const gx_simt_spec *limits, char *log,
+                       size_t log_len);
+/*
  * SIMT-verify a program, compile its warp-level form (as gx_jit_check_simt) and load it.
  * opts->flags must be GX_PROG_JIT: the form exists only as specialised code.  A run of the
  * program treats each 32 consecutive events (from the batch's first) as one warp: the lanes
@@ -459,6 +494,31 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream);
 /* Launch the captured graph on `stream` (async). */
 int gx_batch_launch(gx_batch *b, void *stream);
 int gx_batch_destroy(gx_batch *b);
+/*
+ * Steer the batch's blocks with a scheduling program, the `should_try_steal` hook of
+ * Sec. 4.3.2 (policies such as FixedWork, Greedy and LatencyBudget, Sec. 6).  Call before
+ * gx_batch_plan.  The chunk table is then cut into one contiguous share per block: a
+ * block drains its own share, then, before each chunk it would take from another share,
+ * runs `hook` once (one lane, warp 0) on a GX_SCHED_CTX-byte context (offsets
+ * GX_SCHED_OFF_*, `budget_ns` in the budget field).  R0 != 0 takes the chunk; R0 == 0 ends
+ * the block's work.  Every chunk still runs exactly once, whatever the program answers.
+ *
+ * `hook` must be loaded with GX_PROG_JIT and ctx_size GX_SCHED_CTX, and it must be a
+ * warp-uniform handler (gx_verify_simt with every ctx byte uniform) within `limits`
+ * (nullable: GX_SCHED_MAX_INSNS / _HELPERS / _MEM; `limits->uniform` is ignored).  Every
+ * item's program must be specialised too.  Its maps keep their state across launches
+ * like any program's.  GX_EINVAL for a planned batch or a program that does not qualify,
+ * GX_E_VERIFY if the SIMT check refuses it (`log` explains).
+ */
+int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, char *log,
+                       size_t log_len);
+/*
+ * Synchronise `stream`, then copy the last launch's per-block counters (GX_STEAL_WORDS
+ * u32 per block, indexed GX_STEAL_*) of a batch with a scheduling program to `out`
+ * (`cap_blocks` blocks at most); *n_blocks gets the launch's block count.  GX_EINVAL
+ * without a scheduling program or before gx_batch_plan; GX_ENOSPC if cap_blocks is short.
+ */
+int gx_batch_sched_tally(gx_batch *b, uint32_t *out, uint32_t cap_blocks, uint32_t *n_blocks, void *stream);
 
 /* ---------------------------------------------------------------- served form */
 typedef struct gx_server_opts {

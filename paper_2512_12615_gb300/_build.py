@@ -28,7 +28,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + os.pa
 
 CU_SOURCES = ["interp.cu"]
 CXX_SOURCES = ["verifier.cpp", "decode.cpp", "api.cpp", "batch.cpp", "jit.cpp"]
-HEADERS = ["gx_layout.h", "gx_internal.h", "gx_kernels.h", "gx_runtime.h", "gx_device.cuh", "gx_jit.h"]
+HEADERS = ["gx_layout.h", "gx_internal.h", "gx_kernels.h", "gx_runtime.h", "gx_device.cuh", "gx_jit.h", "gx_steal.cuh"]
 
 
 def _stamp() -> str:
@@ -74,7 +74,7 @@ def _compile(src: str, verbose: bool) -> str:
 
 
 EMBED = [("gx_h", os.path.join(INCLUDE, "gx.h")), ("gx_layout_h", os.path.join(CSRC, "gx_layout.h")),
-         ("gx_device_cuh", os.path.join(CSRC, "gx_device.cuh"))]
+         ("gx_device_cuh", os.path.join(CSRC, "gx_device.cuh")), ("gx_steal_cuh", os.path.join(CSRC, "gx_steal.cuh"))]
 
 
 def _write_embed() -> str:

@@ -34,6 +34,7 @@
 
 #include "gx_kernels.h"
 #include "gx_runtime.h"
+#include "gx_steal.cuh"
 
 using namespace gx;
 
@@ -111,10 +112,17 @@ struct Persist {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     gx::JitKernel *jk = nullptr; /* set: the persistent kernel is a multi-program specialised kernel */
+    /* set: mode 2, blocks own shares of the table and this scheduling program steers stealing */
+    gx_prog *sched = nullptr;
+    uint64_t sched_budget = 0;
+    uint64_t steal_off = 0; /* the per-share claim counters, then the per-block tallies */
 
     unsigned *cursor() { return (unsigned *)dmem; }
     unsigned *nchunks() { return (unsigned *)dmem + 1; }
     gx_chunk *table() { return (gx_chunk *)((uint8_t *)dmem + 256); }
+    uint32_t *steal_next() { return (uint32_t *)((uint8_t *)dmem + steal_off); }
+    uint32_t *steal_tally() { return steal_next() + round_up(grid, 4); }
+    uint64_t steal_bytes() const { return round_up(grid, 4) * 4 + (uint64_t)grid * GX_STEAL_WORDS * 4; }
 
     void release() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -158,13 +166,28 @@ struct Persist {
         grid = (unsigned)(c->sms * occ);
         cap_chunks = std::max<uint64_t>(chunks, 1);
         dbytes = 256 + cap_chunks * sizeof(gx_chunk);
+        steal_off = dbytes;
+        if (sched) dbytes += steal_bytes();
         rc = dalloc(c, dbytes, &dmem);
         if (rc) return rc;
         if (cudaMemset(dmem, 0, 256) != cudaSuccess) return GX_E_CUDA;
+        if (sched) { /* the header of mode 2; the chunk count is written with the table */
+            gx_steal_hdr h;
+            memset(&h, 0, sizeof h);
+            h.shares = grid;
+            h.hook_ctx_size = GX_SCHED_CTX;
+            h.budget_ns = sched_budget;
+            h.hook = (const uint8_t *)sched->dmem;
+            h.next = steal_next();
+            h.tally = steal_tally();
+            if (cudaMemcpy(dmem, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemset(steal_next(), 0, steal_bytes()) != cudaSuccess)
+                return GX_E_CUDA;
+        }
         ExecParams P;
         memset(&P, 0, sizeof P);
         P.image_area = area;
-        P.mode = 1;
+        P.mode = sched ? 2 : 1;
         P.chunks = table();
         P.cursor = cursor();
         P.nchunks_dev = nchunks();
@@ -176,6 +199,7 @@ struct Persist {
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = GX_E_CUDA;
         if (rc == GX_OK) {
             cudaMemsetAsync(cursor(), 0, 4, cs);
+            if (sched) cudaMemsetAsync(steal_next(), 0, steal_bytes(), cs);
             if (jk) jit_launch(*jk, P, grid, block, smem, cs);
             else launch_exec(P, grid, block, smem, cs);
             if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) rc = GX_E_CUDA;
@@ -202,6 +226,8 @@ struct gx_batch {
     gx::JitKernel jk;
     std::map<gx_prog *, uint32_t> slots;
     bool jit = false;
+    gx_prog *sched = nullptr; /* the scheduling program (gx_batch_set_sched) */
+    uint64_t sched_budget = 0;
 };
 
 /* build the batch's multi-program kernel when every item's program is specialised */
@@ -212,7 +238,7 @@ static int batch_jit(gx_batch *b) {
     if (!b->jit) {
         for (auto &it : b->items)
             if (it.prog->jp.warp) return GX_EINVAL; /* a warp-level program exists only as specialised code */
-        return GX_OK;
+        return b->sched ? GX_EINVAL : GX_OK; /* so does the work-stealing kernel */
     }
     std::vector<const gx::JitProgram *> progs;
     b->slots.clear();
@@ -222,7 +248,7 @@ static int batch_jit(gx_batch *b) {
             progs.push_back(&it.prog->jp);
         }
     std::string log;
-    int rc = gx::jit_build(progs, b->jk, log);
+    int rc = gx::jit_build(progs, b->jk, log, b->sched ? &b->sched->jp : nullptr);
     if (rc) b->jit = false;
     return rc;
 }
@@ -304,6 +330,8 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t 
     /* one kernel holds every program: a wide cache would cost all of them occupancy */
     alloc = std::min(alloc, dflt);
     b->persist.jk = b->jit ? &b->jk : nullptr;
+    b->persist.sched = b->sched;
+    b->persist.sched_budget = b->sched_budget;
     make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr, use_pref ? dflt : 0,
                 area_bits(b->persist.jk, shards, alloc));
     int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size(), shards, alloc);
@@ -338,6 +366,9 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
     std::vector<gx_map *> maps;
     for (auto &it : b->items)
         for (auto *m : it.prog->maps)
+            if (std::find(maps.begin(), maps.end(), m) == maps.end()) maps.push_back(m);
+    if (b->sched)
+        for (auto *m : b->sched->maps)
             if (std::find(maps.begin(), maps.end(), m) == maps.end()) maps.push_back(m);
     std::vector<void *> saved(maps.size(), nullptr);
     int rc = GX_OK;
@@ -398,9 +429,41 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
 int gx_batch_launch(gx_batch *b, void *stream) {
     if (!b || !b->planned) return GX_EINVAL;
     int rc = b->persist.launch((cudaStream_t)stream);
-    if (rc == GX_OK)
+    if (rc == GX_OK) {
         for (auto &it : b->items) it.prog->launches++;
+        if (b->sched) b->sched->launches++;
+    }
     return rc;
+}
+
+int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, char *log,
+                       size_t log_len) {
+    if (!b || !hook || hook->ctx != b->ctx || b->planned || !hook->jit || hook->jp.warp) return GX_EINVAL;
+    gx::VerifyOut v;
+    const gx::JitProgram &jp = hook->jp;
+    int rc = gx::check_sched_program(jp.insns.data(), (uint32_t)jp.insns.size(), jp.maps.data(),
+                                     (uint32_t)jp.maps.size(), hook->opts, limits, v);
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, v.log.size());
+        memcpy(log, v.log.data(), k);
+        log[k] = 0;
+    }
+    if (rc) return rc;
+    b->sched = hook;
+    b->sched_budget = budget_ns;
+    return GX_OK;
+}
+
+int gx_batch_sched_tally(gx_batch *b, uint32_t *out, uint32_t cap_blocks, uint32_t *n_blocks, void *stream) {
+    if (!b || !b->sched || !b->planned || !n_blocks || (cap_blocks && !out)) return GX_EINVAL;
+    const uint32_t g = b->persist.grid;
+    *n_blocks = g;
+    if (cap_blocks < g) return GX_ENOSPC;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+        cudaMemcpy(out, b->persist.steal_tally(), (size_t)g * GX_STEAL_WORDS * 4, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return GX_E_CUDA;
+    return GX_OK;
 }
 
 int gx_batch_destroy(gx_batch *b) {

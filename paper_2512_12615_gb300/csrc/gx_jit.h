@@ -67,8 +67,19 @@ struct ShardPlan {
 };
 ShardPlan plan_shards(const JitProgram &p);
 
-/* compile (or fetch from the caches) one kernel running progs[slot] for chunk slot `slot` */
-int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log);
+/*
+ * compile (or fetch from the caches) one kernel running progs[slot] for chunk slot `slot`;
+ * with `sched`, the kernel is the work-stealing form steered by that scheduling program
+ */
+int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log,
+              const JitProgram *sched = nullptr);
+/*
+ * Is this program fit to steer a batch (gx_batch_set_sched)?  ctx_size GX_SCHED_CTX and a
+ * warp-uniform handler within `limits` (nullable: the GX_SCHED_MAX_* budget).  GX_OK,
+ * GX_EINVAL or GX_E_VERIFY; `v` gets the verifier's findings.
+ */
+int check_sched_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                        const gx_prog_opts &opts, const gx_simt_spec *limits, VerifyOut &v);
 cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
                        cudaStream_t s, bool capped = false);
 cudaError_t jit_set_smem(JitKernel &k, size_t bytes);

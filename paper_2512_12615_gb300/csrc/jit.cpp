@@ -33,6 +33,7 @@
 extern "C" const char gx_embed_gx_h[];
 extern "C" const char gx_embed_gx_layout_h[];
 extern "C" const char gx_embed_gx_device_cuh[];
+extern "C" const char gx_embed_gx_steal_cuh[];
 
 namespace gx {
 namespace {
@@ -702,15 +703,25 @@ void write_file(const std::string &path, const std::vector<char> &data) {
 
 } // namespace
 
-std::string jit_source(const std::vector<const JitProgram *> &progs, std::string &log, int &rc) {
+std::string jit_source(const std::vector<const JitProgram *> &progs, std::string &log, int &rc,
+                       const JitProgram *sched = nullptr) {
     std::string src;
-    src += "#include \"gx_device.cuh\"\nnamespace gx {\n";
+    src += "#include \"gx_device.cuh\"\n";
+    if (sched) src += "#include \"gx_steal.cuh\"\n";
+    src += "namespace gx {\n";
     rc = GX_OK;
     for (size_t i = 0; i < progs.size() && rc == GX_OK; i++) {
         const ShardPlan sp = plan_shards(*progs[i]);
         rc = gen_body(*progs[i], sp, (int)i, src, log);
         src += gen_wc_init(sp, (int)i);
         src += gen_wc_flush(sp, (int)i);
+    }
+    /* the scheduling program: per-lane code with no combining, out of line (run rarely, by warp 0) */
+    const std::string hs = std::to_string(progs.size());
+    if (sched && rc == GX_OK) {
+        rc = gen_body(*sched, ShardPlan{}, (int)progs.size(), src, log);
+        src += "__device__ __noinline__ u64 gx_sched_call(const ExecEnv &e, const u64 *c, bool v, u64 x) {\n"
+               "  return gx_body_" + hs + "(e, c, v, x);\n}\n";
     }
     auto hook = [&](const char *what) {
         std::string h = std::string("  [](const gx::ExecEnv &env) {\n");
@@ -740,7 +751,8 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
                    "  extern __shared__ __align__(16) uint8_t smem[];\n"
                    "  const ExecEnv env = stage_env_at(smem, shard_off, (u32)ch.pad, wcp);\n  " +
                    chunk_loop(i) + "\n}\n";
-    std::string body = "  gx::exec_tiles(P, [](const gx::ExecEnv &env, const gx_chunk &ch, gx::u64 *ctx_all) {\n";
+    std::string body = std::string("  gx::") + (sched ? "exec_steal" : "exec_tiles") +
+                       "(P, [](const gx::ExecEnv &env, const gx_chunk &ch, gx::u64 *ctx_all) {\n";
     if (progs.size() == 1) {
         body += "    using namespace gx;\n    " + chunk_loop(0) + "\n";
     } else {
@@ -750,7 +762,11 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
                     "(ch, env.wc_bits | (env.wc_agg << 8), (gx::u32)(env.shard - smem_base), ctx_all); break;\n";
         body += "    }\n";
     }
-    body += "  },\n" + hook("init") + ",\n" + hook("flush") + ");\n}\n";
+    body += "  },\n" + hook("init") + ",\n" + hook("flush");
+    if (sched)
+        body += ",\n  [](const gx::ExecEnv &e, const gx::u64 *c, bool v, gx::u64 x) -> gx::u64 { return "
+                "gx::gx_sched_call(e, c, v, x); }";
+    body += ");\n}\n";
     src += "} // namespace gx\n\n";
     /*
      * One program: a wide entry (registers as the compiler likes) and a capped one (at most
@@ -782,10 +798,10 @@ int jit_cubin(const std::string &src, const std::string &key, std::vector<char> 
         log = "jit: " + nv.err;
         return GX_E_NODEV;
     }
-    const char *hdrs[] = {gx_embed_gx_h, gx_embed_gx_layout_h, gx_embed_gx_device_cuh};
-    const char *names[] = {"gx.h", "gx_layout.h", "gx_device.cuh"};
+    const char *hdrs[] = {gx_embed_gx_h, gx_embed_gx_layout_h, gx_embed_gx_device_cuh, gx_embed_gx_steal_cuh};
+    const char *names[] = {"gx.h", "gx_layout.h", "gx_device.cuh", "gx_steal.cuh"};
     nvrtcProgram_ prog = nullptr;
-    if (nv.create(&prog, src.c_str(), "gx_prog.cu", 3, hdrs, names) != 0) {
+    if (nv.create(&prog, src.c_str(), "gx_prog.cu", 4, hdrs, names) != 0) {
         log = "jit: nvrtcCreateProgram failed";
         return GX_E_CUDA;
     }
@@ -813,12 +829,13 @@ int jit_cubin(const std::string &src, const std::string &key, std::vector<char> 
 }
 
 std::string jit_key(const std::string &src) {
-    return fnv_hex(src + gx_embed_gx_device_cuh + gx_embed_gx_layout_h + gx_embed_gx_h);
+    return fnv_hex(src + gx_embed_gx_device_cuh + gx_embed_gx_layout_h + gx_embed_gx_h + gx_embed_gx_steal_cuh);
 }
 
-int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log) {
+int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std::string &log,
+              const JitProgram *sched) {
     int rc;
-    const std::string src = jit_source(progs, log, rc);
+    const std::string src = jit_source(progs, log, rc, sched);
     if (rc) return rc;
     out.shard_bytes = 0;
     out.wc_max_bits = 0;
@@ -859,6 +876,24 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
     out.kernel_capped = c.kernel_capped;
     out.key = key;
     return GX_OK;
+}
+
+int check_sched_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                        const gx_prog_opts &opts, const gx_simt_spec *limits, VerifyOut &v) {
+    if (opts.ctx_size != GX_SCHED_CTX) {
+        v.log = "scheduling program: ctx_size must be " + std::to_string(GX_SCHED_CTX);
+        return GX_EINVAL;
+    }
+    if (limits && limits->reserved) {
+        v.log = "scheduling program: limits->reserved must be 0";
+        return GX_EINVAL;
+    }
+    SimtIn in;
+    in.uniform.assign(GX_SCHED_CTX, 1); /* every field is the same for the block's threads */
+    in.max_insns = limits ? limits->max_insns : GX_SCHED_MAX_INSNS;
+    in.max_helpers = limits ? limits->max_helper_calls : GX_SCHED_MAX_HELPERS;
+    in.max_mem = limits ? limits->max_mem_ops : GX_SCHED_MAX_MEM;
+    return verify_program(insns, n, maps, n_maps, opts, v, &in);
 }
 
 cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
@@ -927,6 +962,44 @@ extern "C" int gx_jit_check_simt(const uint64_t *insns, uint32_t n, const gx_map
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
         jp.warp = true;
         const std::string src = gx::jit_source({&jp}, msg, rc);
+        std::vector<char> cubin;
+        if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);
+    }
+    if (log && log_len) {
+        size_t k = std::min(log_len - 1, msg.size());
+        memcpy(log, msg.data(), k);
+        log[k] = 0;
+    }
+    return rc;
+}
+
+extern "C" int gx_jit_check_sched(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                                  const gx_prog_opts *opts, const uint64_t *hook, uint32_t n_hook,
+                                  const gx_map_spec *hook_maps, uint32_t n_hook_maps, const gx_prog_opts *hook_opts,
+                                  const gx_simt_spec *limits, char *log, size_t log_len) {
+    if (!insns || !opts || (n_maps && !maps) || !hook || !hook_opts || (n_hook_maps && !hook_maps)) return GX_EINVAL;
+    gx::VerifyOut v, hv;
+    int rc = gx::verify_program(insns, n, maps, n_maps, *opts, v);
+    std::string msg = v.log;
+    if (rc == GX_OK) {
+        rc = gx::check_sched_program(hook, n_hook, hook_maps, n_hook_maps, *hook_opts, limits, hv);
+        msg = hv.log;
+    }
+    if (rc == GX_OK) {
+        gx::JitProgram jp, hp;
+        jp.insns.assign(insns, insns + n);
+        jp.info = v.info;
+        jp.maps.assign(maps, maps + n_maps);
+        jp.use = v.map_use;
+        jp.ctx_size = opts->ctx_size;
+        jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        hp.insns.assign(hook, hook + n_hook);
+        hp.info = hv.info;
+        hp.maps.assign(hook_maps, hook_maps + n_hook_maps);
+        hp.use = hv.map_use;
+        hp.ctx_size = hook_opts->ctx_size;
+        hp.budget = hook_opts->insn_budget ? hook_opts->insn_budget : (1ull << 16);
+        const std::string src = gx::jit_source({&jp}, msg, rc, &hp);
         std::vector<char> cubin;
         if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);
     }

@@ -67,6 +67,14 @@ class SimtReport(ctypes.Structure):
  SIMT_V_INSNS, SIMT_V_HELPERS, SIMT_V_MEM) = range(11)
 
 
+# scheduling programs (gx_batch_set_sched): context layout, default hook budget, per-block tallies
+SCHED_CTX = 32
+SCHED_OFF_BLOCK, SCHED_OFF_SM, SCHED_OFF_DONE, SCHED_OFF_LEFT, SCHED_OFF_ELAPSED, SCHED_OFF_BUDGET = 0, 4, 8, 12, 16, 24
+SCHED_MAX_INSNS, SCHED_MAX_HELPERS, SCHED_MAX_MEM = 64, 2, 16
+STEAL_OWNED, STEAL_STOLEN, STEAL_ASKED, STEAL_GRANTED = range(4)
+STEAL_WORDS = 4
+
+
 SHARDS_OFF = 255
 SHARDS_AGG = 0x100  # OR into a width: warp-aggregate the updates that miss the combining cache
 
@@ -125,6 +133,9 @@ _SIGS = {
                              ctypes.POINTER(SimtSpec), ctypes.POINTER(SimtReport), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_jit_check_simt": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
                                 ctypes.POINTER(SimtSpec), ctypes.c_char_p, ctypes.c_size_t]),
+    "gx_jit_check_sched": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                                 ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts),
+                                 ctypes.POINTER(SimtSpec), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_merge_ops": (i32, [ctypes.c_void_p, u32, ctypes.POINTER(MapSpec), u32, ctypes.POINTER(ProgOpts), u32,
                            ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(u32), ctypes.c_char_p, ctypes.c_size_t]),
     "gx_verify_load": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(ctypes.c_void_p), u32,
@@ -146,6 +157,9 @@ _SIGS = {
     "gx_batch_plan": (i32, [ctypes.c_void_p, ctypes.POINTER(Launch), ctypes.c_void_p]),
     "gx_batch_launch": (i32, [ctypes.c_void_p, ctypes.c_void_p]),
     "gx_batch_destroy": (i32, [ctypes.c_void_p]),
+    "gx_batch_set_sched": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(SimtSpec), ctypes.c_char_p,
+                                 ctypes.c_size_t]),
+    "gx_batch_sched_tally": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(u32), ctypes.c_void_p]),
     "gx_server_create": (i32, [ctypes.c_void_p, ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)]),
     "gx_server_submit": (i32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p, u64, dbl]),
     "gx_server_replay": (i32, [ctypes.c_void_p, ctypes.POINTER(Request), u32, dbl]),
@@ -277,6 +291,33 @@ def jit_check_simt(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, 
     rc = lib().gx_jit_check_simt(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
                                  ctypes.byref(spec), log, 1 << 20)
     del keep
+    return rc, log.value.decode()
+
+
+def _sched_limits(max_insns: Optional[int], max_helper_calls: Optional[int], max_mem_ops: Optional[int]):
+    """A hook budget, or None for the library's default (GX_SCHED_MAX_*)."""
+    if max_insns is None and max_helper_calls is None and max_mem_ops is None:
+        return None
+    return SimtSpec(None, SCHED_MAX_INSNS if max_insns is None else max_insns,
+                    SCHED_MAX_HELPERS if max_helper_calls is None else max_helper_calls,
+                    SCHED_MAX_MEM if max_mem_ops is None else max_mem_ops, 0)
+
+
+def jit_check_sched(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, hook: np.ndarray,
+                    hook_specs: Sequence[dict], *, deterministic: bool = False, max_insns: Optional[int] = None,
+                    max_helper_calls: Optional[int] = None, max_mem_ops: Optional[int] = None) -> Tuple[int, str]:
+    """Host-only (gx_jit_check_sched): compile the work-stealing batch kernel of one program
+    steered by the scheduling program `hook`: (status, log)."""
+    insns = np.ascontiguousarray(insns, dtype=np.uint64)
+    hook = np.ascontiguousarray(hook, dtype=np.uint64)
+    specs, hspecs = _specs(map_specs), _specs(hook_specs)
+    opts = ProgOpts(ctx_size, int(deterministic), 0, 0, 0)
+    hopts = ProgOpts(SCHED_CTX, 0, 0, 0, 0)
+    lim = _sched_limits(max_insns, max_helper_calls, max_mem_ops)
+    log = ctypes.create_string_buffer(1 << 20)
+    rc = lib().gx_jit_check_sched(insns.ctypes.data, insns.size, specs, len(map_specs), ctypes.byref(opts),
+                                  hook.ctypes.data, hook.size, hspecs, len(hook_specs), ctypes.byref(hopts),
+                                  None if lim is None else ctypes.byref(lim), log, 1 << 20)
     return rc, log.value.decode()
 
 
@@ -468,6 +509,27 @@ class Batch:
 
     def launch(self, stream=None) -> None:
         check(lib().gx_batch_launch(self.h, _stream(stream)), "gx_batch_launch")
+
+    def set_sched(self, hook: Program, budget_ns: int = 0, *, max_insns: Optional[int] = None,
+                  max_helper_calls: Optional[int] = None, max_mem_ops: Optional[int] = None) -> None:
+        """Steer the blocks with a scheduling program (gx_batch_set_sched); before plan()."""
+        lim = _sched_limits(max_insns, max_helper_calls, max_mem_ops)
+        log = ctypes.create_string_buffer(1 << 16)
+        rc = lib().gx_batch_set_sched(self.h, hook.h, budget_ns, None if lim is None else ctypes.byref(lim), log,
+                                      1 << 16)
+        check(rc, "gx_batch_set_sched: " + log.value.decode())
+        self._sched = hook
+
+    def sched_tally(self, stream=None) -> np.ndarray:
+        """The last launch's per-block counters (gx_batch_sched_tally): uint32 [blocks, STEAL_WORDS]."""
+        n = u32(0)
+        rc = lib().gx_batch_sched_tally(self.h, None, 0, ctypes.byref(n), _stream(stream))
+        if rc not in (OK, ENOSPC):
+            check(rc, "gx_batch_sched_tally")
+        out = np.zeros((max(1, n.value), STEAL_WORDS), dtype=np.uint32)
+        check(lib().gx_batch_sched_tally(self.h, out.ctypes.data, n.value, ctypes.byref(n), _stream(stream)),
+              "gx_batch_sched_tally")
+        return out[:n.value]
 
     def destroy(self) -> None:
         if self.h:

@@ -313,3 +313,61 @@ def test_per_lane_form_has_no_collectives_of_its_own(tmp_path, monkeypatch):
         body = f.read_text().split("} // namespace gx")[0]  # the program bodies, before the entry points
         assert "_sync(" not in body, f.name
         assert "__activemask()" in body or "agg_update" not in body, f.name
+
+
+# ---------------------------------------------------------------- work stealing (compile only)
+SCHED_KINDS = ["fixed", "greedy", "latency_budget"]
+
+
+def _check_sched(prog, specs, cs, hook, hook_specs, **kw):
+    rc, log = gx.jit_check_sched(prog, specs, cs, hook, hook_specs, deterministic=True, **kw)
+    if rc == gx.E_NODEV:
+        pytest.skip("no runtime compiler on this host")
+    assert rc == 0, log
+
+
+@pytest.mark.parametrize("kind", SCHED_KINDS)
+def test_stealing_kernel_compiles(kind):
+    """The persistent kernel of mode 2 (shares, a scheduling program asked before each
+    stolen chunk) compiles for sm_103a with each policy steering it."""
+    hook, hook_specs, _ = P.sched_policy(kind)
+    for build in (P.counting, P.page_heat):
+        _check_sched(*build(), hook, hook_specs)
+    _check_sched(*P.batch_programs()[9], hook, hook_specs)
+
+
+def test_scheduling_program_must_qualify():
+    """The hook context is 32 warp-uniform bytes; a program over the hook budget is refused
+    with the budget named, and one with another context size is not a scheduling program."""
+    prog, specs, cs = P.counting()
+    hook, hook_specs, _ = P.sched_policy("latency_budget")  # worst path: 22 insns, 1 call, 7 memory ops
+    rc, log = gx.jit_check_sched(prog, specs, cs, hook, hook_specs, max_insns=21)
+    assert rc == gx.E_VERIFY, log
+    rc, log = gx.jit_check_sched(prog, specs, cs, hook, hook_specs, max_mem_ops=6)
+    assert rc == gx.E_VERIFY, log
+    _check_sched(prog, specs, cs, hook, hook_specs, max_insns=22, max_helper_calls=1, max_mem_ops=7)
+    # the scheduling program's context is GX_SCHED_CTX bytes: a 64-byte reader is not one
+    reader = assemble(["ldx8 r0 r1 56", "exit"]).prog()
+    rc, log = gx.jit_check_sched(prog, specs, cs, reader, [])
+    assert rc in (gx.E_VERIFY, gx.EINVAL), log
+
+
+def test_stealing_source_shape(tmp_path, monkeypatch):
+    """Only a batch with a scheduling program gets the stealing skeleton: its source holds
+    one out-of-line scheduling call, the skeleton in every entry point, and the hook's body
+    has no collective of its own.  Sources without one never include the header."""
+    monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path / "sched"))
+    hook, hook_specs, _ = P.sched_policy("greedy")
+    _check_sched(*P.page_heat(), hook, hook_specs)
+    (src,) = list((tmp_path / "sched").glob("*.cu"))
+    text = src.read_text()
+    assert text.count('#include "gx_steal.cuh"') == 1
+    assert text.count("__device__ __noinline__ u64 gx_sched_call(") == 1
+    assert text.count("gx::exec_steal(P,") == 2 and "gx::exec_tiles(" not in text  # wide and capped entries
+    body = text.split("__device__ __noinline__ u64 gx_sched_call(")[0].split("gx_body_1(")[1]
+    assert "_sync(" not in body
+    monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path / "plain"))
+    _check(*P.page_heat())
+    (plain,) = list((tmp_path / "plain").glob("*.cu"))
+    ptext = plain.read_text()
+    assert "gx_steal" not in ptext and "gx_sched_call" not in ptext and "exec_steal" not in ptext
