@@ -10,7 +10,7 @@
  *   - every walk ends, within its own share + one failed claim per share of claims.
  * Prints OK or the failed checks.
  */
-#include "../../paper_2512_12615_gb300/csrc/gx_steal.cuh"
+#include "gx_steal.cuh" /* compiled with the engine's csrc/ (or a mutant copy) on the include path */
 
 #include <atomic>
 #include <cstdio>
