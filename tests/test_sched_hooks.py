@@ -2,7 +2,9 @@
 Greedy / LatencyBudget schedulers of Sec. 6), host side: their decisions on the oracle
 equal the closed forms; they are warp-uniform handlers within a hook budget, whose worst
 paths are counted by hand; their statistics are order-independent (deterministic mode).
-Running them inside the persistent kernel's claim loop is device work not built yet.
+On the device they steer a batch's stealing mode (gx_batch_set_sched): its walk is pinned in
+tests/test_host_steal.py, its kernel compiles in tests/test_jit_compile.py, and its GPU
+parity tests (tests/test_gpu_sched.py) have not yet run.
 """
 import numpy as np
 import pytest
