@@ -507,7 +507,8 @@ int gx_batch_destroy(gx_batch *b);
  * warp-uniform handler (gx_verify_simt with every ctx byte uniform) within `limits`
  * (nullable: GX_SCHED_MAX_INSNS / _HELPERS / _MEM; `limits->uniform` is ignored).  Every
  * item's program must be specialised too.  Its maps keep their state across launches
- * like any program's.  GX_EINVAL for a planned batch or a program that does not qualify,
+ * like any program's, and it must stay loaded while the batch exists (as the items'
+ * programs must).  GX_EINVAL for a planned batch or a program that does not qualify,
  * GX_E_VERIFY if the SIMT check refuses it (`log` explains).
  */
 int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, char *log,

@@ -349,7 +349,8 @@ def test_scheduling_program_must_qualify():
     # the scheduling program's context is GX_SCHED_CTX bytes: a 64-byte reader is not one
     reader = assemble(["ldx8 r0 r1 56", "exit"]).prog()
     rc, log = gx.jit_check_sched(prog, specs, cs, reader, [])
-    assert rc in (gx.E_VERIFY, gx.EINVAL), log
+    assert rc == gx.E_VERIFY and "ctx" in log, log
+    _check_sched(prog, specs, cs, assemble(["ldx8 r0 r1 24", "exit"]).prog(), [])  # the budget field
 
 
 def test_stealing_source_shape(tmp_path, monkeypatch):
