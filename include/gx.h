@@ -502,6 +502,7 @@ int gx_batch_destroy(gx_batch *b);
  * runs `hook` once (one lane, warp 0) on a GX_SCHED_CTX-byte context (offsets
  * GX_SCHED_OFF_*, `budget_ns` in the budget field).  R0 != 0 takes the chunk; R0 == 0 ends
  * the block's work.  Every chunk still runs exactly once, whatever the program answers.
+ * Ring-buffer records the program writes carry the block index as their event index.
  *
  * `hook` must be loaded with GX_PROG_JIT and ctx_size GX_SCHED_CTX, and it must be a
  * warp-uniform handler (gx_verify_simt with every ctx byte uniform) within `limits`

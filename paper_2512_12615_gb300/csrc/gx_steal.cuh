@@ -47,6 +47,10 @@ typedef struct gx_steal_hdr {
 
 #ifdef __cplusplus
 static_assert(sizeof(gx_steal_hdr) == 256, "the persistent header block is 256 bytes");
+/* exec_steal packs the context as four words: block | SM << 32, done | left << 32, elapsed, budget */
+static_assert(GX_SCHED_CTX == 32 && GX_SCHED_OFF_BLOCK == 0 && GX_SCHED_OFF_SM == 4 && GX_SCHED_OFF_DONE == 8 &&
+                  GX_SCHED_OFF_LEFT == 12 && GX_SCHED_OFF_ELAPSED == 16 && GX_SCHED_OFF_BUDGET == 24,
+              "scheduling context layout");
 #endif
 
 namespace gx {

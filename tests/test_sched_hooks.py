@@ -82,3 +82,14 @@ def test_oracle_max_path_is_the_counted_one():
     ctx["left"], ctx["elapsed"], ctx["budget"] = 3, 10, 1_000_000
     _, count = O.run(prog, O.maps_from_specs(specs), ctx, cs)
     assert count == WORST["latency_budget"][0]
+
+
+def test_context_layout_is_the_engines():
+    """The policies read the fields where the engine's stealing kernel writes them."""
+    assert P.SCHED_CTX == gx.SCHED_CTX
+    assert (P.SCHED_BLOCK, P.SCHED_SM, P.SCHED_DONE, P.SCHED_LEFT, P.SCHED_ELAPSED, P.SCHED_BUDGET) == (
+        gx.SCHED_OFF_BLOCK, gx.SCHED_OFF_SM, gx.SCHED_OFF_DONE, gx.SCHED_OFF_LEFT, gx.SCHED_OFF_ELAPSED,
+        gx.SCHED_OFF_BUDGET)
+    # the default hook budget holds all three policies
+    for kind in WORST:
+        assert all(w <= m for w, m in zip(WORST[kind], (gx.SCHED_MAX_INSNS, gx.SCHED_MAX_HELPERS, gx.SCHED_MAX_MEM)))
