@@ -352,9 +352,9 @@ int gx_verify_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *m
 int gx_jit_check_simt(const uint64_t *insns, uint32_t n_insns, const gx_map_spec *maps, uint32_t n_maps,
                       const gx_prog_opts *opts, const gx_simt_spec *simt, char *log, size_t log_len);
 /*
- * Host only: compile, without loading it, the persistent kernel of a batch whose one
- * program (insns, maps, opts) runs under the scheduling program (hook, hook_maps,
- * hook_opts) as gx_batch_set_sched describes.  Both must verify; the hook must pass the
+ * Host only: compile, without loading it, the stealing kernel (both modes of
+ * gx_batch_set_sched) of a batch whose one program (insns, maps, opts) runs under the
+ * scheduling program (hook, hook_maps, hook_opts).  Both must verify; the hook must pass the
  * SIMT check within `limits` (nullable: the GX_SCHED_MAX_* budget) and have ctx_size
  * GX_SCHED_CTX.  0, GX_E_VERIFY, GX_EINVAL, GX_E_NODEV or GX_E_CUDA; `log` explains.
  */
@@ -512,8 +512,19 @@ int gx_batch_destroy(gx_batch *b);
  * programs must).  GX_EINVAL for a planned batch or a program that does not qualify,
  * GX_E_VERIFY if the SIMT check refuses it (`log` explains).
  */
-int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, char *log,
-                       size_t log_len);
+int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, uint32_t flags,
+                       char *log, size_t log_len);
+/*
+ * gx_batch_set_sched flags.  GX_SCHED_F_LAUNCH_CONTROL: instead of persistent blocks with
+ * shares, launch one block per chunk; a block that has run its chunk asks `hook` and, on
+ * R0 != 0, cancels a block that has not started yet (cluster launch control) and runs
+ * that block's chunk.  The context's "left" field is the number of chunks not yet
+ * started.  A cancelled block never runs, so every chunk still runs exactly once; a cancel
+ * whose response does not come within the wait bound ends that block's stealing and sets
+ * the scheduling program's status to GX_E_TIMEOUT (the chunk it may have cancelled is then
+ * lost).  Tallies are per launched block; cancelled blocks' rows stay zero.
+ */
+#define GX_SCHED_F_LAUNCH_CONTROL 1u
 /*
  * Synchronise `stream`, then copy the last launch's per-block counters (GX_STEAL_WORDS
  * u32 per block, indexed GX_STEAL_*) of a batch with a scheduling program to `out`

@@ -12,6 +12,6 @@ from .gx import (  # noqa: F401
     MERGE_ADD, MERGE_AND, MERGE_MAX, MERGE_MIN, MERGE_NONE, MERGE_OR, MERGE_W8, MERGE_XOR, merge_ops,
     SCHED_CTX, SCHED_MAX_HELPERS, SCHED_MAX_INSNS, SCHED_MAX_MEM, SCHED_OFF_BLOCK, SCHED_OFF_BUDGET,
     SCHED_OFF_DONE, SCHED_OFF_ELAPSED, SCHED_OFF_LEFT, SCHED_OFF_SM, STEAL_ASKED, STEAL_GRANTED, STEAL_OWNED,
-    STEAL_STOLEN, STEAL_WORDS, jit_check_sched,
+    STEAL_STOLEN, STEAL_WORDS, SCHED_F_LAUNCH_CONTROL, jit_check_sched,
 )
 from . import merge  # noqa: F401,E402

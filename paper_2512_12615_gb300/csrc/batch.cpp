@@ -115,6 +115,7 @@ struct Persist {
     /* set: mode 2, blocks own shares of the table and this scheduling program steers stealing */
     gx_prog *sched = nullptr;
     uint64_t sched_budget = 0;
+    bool launch_control = false; /* mode 3: one block per chunk, stealing by cancelling blocks not yet started */
     uint64_t steal_off = 0; /* the per-share claim counters, then the per-block tallies */
 
     unsigned *cursor() { return (unsigned *)dmem; }
@@ -164,6 +165,7 @@ struct Persist {
             return GX_E_CUDA;
         }
         grid = (unsigned)(c->sms * occ);
+        if (sched && launch_control) grid = (unsigned)std::max<uint64_t>(chunks, 1);
         cap_chunks = std::max<uint64_t>(chunks, 1);
         dbytes = 256 + cap_chunks * sizeof(gx_chunk);
         steal_off = dbytes;
@@ -187,7 +189,7 @@ struct Persist {
         ExecParams P;
         memset(&P, 0, sizeof P);
         P.image_area = area;
-        P.mode = sched ? 2 : 1;
+        P.mode = sched ? (launch_control ? 3 : 2) : 1;
         P.chunks = table();
         P.cursor = cursor();
         P.nchunks_dev = nchunks();
@@ -228,6 +230,7 @@ struct gx_batch {
     bool jit = false;
     gx_prog *sched = nullptr; /* the scheduling program (gx_batch_set_sched) */
     uint64_t sched_budget = 0;
+    uint32_t sched_flags = 0;
 };
 
 /* build the batch's multi-program kernel when every item's program is specialised */
@@ -332,6 +335,7 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t 
     b->persist.jk = b->jit ? &b->jk : nullptr;
     b->persist.sched = b->sched;
     b->persist.sched_budget = b->sched_budget;
+    b->persist.launch_control = (b->sched_flags & GX_SCHED_F_LAUNCH_CONTROL) != 0;
     make_chunks(b->items, (uint64_t)block * ept, b->chunks, b->jit ? &b->slots : nullptr, use_pref ? dflt : 0,
                 area_bits(b->persist.jk, shards, alloc));
     int rc = b->persist.build(b->ctx, block, area, max_ctx, b->chunks.size(), shards, alloc);
@@ -436,9 +440,10 @@ int gx_batch_launch(gx_batch *b, void *stream) {
     return rc;
 }
 
-int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, char *log,
-                       size_t log_len) {
+int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_simt_spec *limits, uint32_t flags,
+                       char *log, size_t log_len) {
     if (!b || !hook || hook->ctx != b->ctx || b->planned || !hook->jit || hook->jp.warp) return GX_EINVAL;
+    if (flags & ~GX_SCHED_F_LAUNCH_CONTROL) return GX_EINVAL;
     gx::VerifyOut v;
     const gx::JitProgram &jp = hook->jp;
     int rc = gx::check_sched_program(jp.insns.data(), (uint32_t)jp.insns.size(), jp.maps.data(),
@@ -451,6 +456,7 @@ int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_
     if (rc) return rc;
     b->sched = hook;
     b->sched_budget = budget_ns;
+    b->sched_flags = flags;
     return GX_OK;
 }
 

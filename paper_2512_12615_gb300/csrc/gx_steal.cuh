@@ -40,8 +40,9 @@ typedef struct gx_steal_hdr {
     uint32_t hook_ctx_size; /* GX_SCHED_CTX */
     uint64_t budget_ns;     /* the context's budget field */
     const uint8_t *hook;    /* the scheduling program's device image */
-    uint32_t *next;         /* per share: claims so far; zeroed before each launch */
-    uint32_t *tally;        /* per block: GX_STEAL_WORDS counters; zeroed before each launch */
+    uint32_t *next;         /* mode 2: per share, claims so far; mode 3: next[0] = chunks started;
+                               zeroed before each launch */
+    uint32_t *tally;        /* per block of the launch: GX_STEAL_WORDS counters; zeroed before each launch */
     uint64_t pad[26];
 } gx_steal_hdr;
 
@@ -94,6 +95,32 @@ GX_STEAL_FN void steal_walk(uint32_t self, uint32_t shares, uint32_t n, Claim cl
     }
 }
 
+/*
+ * One block's walk when every chunk has a block of its own (mode 3): run the block's own
+ * chunk, then, while left() (chunks not yet started) is nonzero and ask(left, done) says
+ * yes, cancel() a block that has not started and run its chunk.  cancel() returns that
+ * block's index, or a value >= n when no block was cancelled; after that the walk never
+ * cancels again.
+ */
+template <class Left, class Ask, class Cancel, class Run>
+GX_STEAL_FN void cancel_walk(uint32_t self, uint32_t n, Left left, Ask ask, Cancel cancel, Run run, uint32_t *t) {
+    if (self < n) {
+        run(self);
+        t[GX_STEAL_OWNED]++;
+    }
+    for (;;) {
+        const uint32_t l = left();
+        if (l == 0) break;
+        t[GX_STEAL_ASKED]++;
+        if (!ask(l, t[GX_STEAL_OWNED] + t[GX_STEAL_STOLEN])) break;
+        t[GX_STEAL_GRANTED]++;
+        const uint32_t c = cancel();
+        if (c >= n) break;
+        run(c);
+        t[GX_STEAL_STOLEN]++;
+    }
+}
+
 } // namespace gx
 
 #ifdef __CUDACC__
@@ -114,12 +141,67 @@ __device__ __forceinline__ u32 steal_smid() {
 }
 
 /*
- * The persistent skeleton of mode 2: exec_tiles' chunk handling (restaging on a program
+ * Bounded wait on phase `parity` of a shared-memory mbarrier; false if it gave up.
+ */
+__device__ __forceinline__ bool steal_mbar_wait(u32 mbar, u32 parity) {
+    for (u32 i = 0; i < WAIT_SPINS; i++) {
+        u32 ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+/*
+ * Ask the hardware to cancel one block of this launch that has not started (cluster launch
+ * control; every block is a cluster of one).  Thread 0 only.  Returns the cancelled block's
+ * index, GX_STEAL_NONE if none was left, or GX_STEAL_STUCK if the response did not arrive
+ * within the wait bound.  After a GX_STEAL_NONE the block must not ask again.
+ */
+#define GX_STEAL_NONE 0xFFFFFFFFu
+#define GX_STEAL_STUCK 0xFFFFFFFEu
+__device__ __forceinline__ u32 steal_cancel_one(u32 resp, u32 mbar, u32 parity) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], 16;\n}" ::"r"(mbar)
+                 : "memory");
+    asm volatile("clusterlaunchcontrol.try_cancel.async.shared::cta.mbarrier::complete_tx::bytes.b128 [%0], [%1];" ::"r"(
+                     resp),
+                 "r"(mbar)
+                 : "memory");
+    if (!steal_mbar_wait(mbar, parity)) return GX_STEAL_STUCK;
+    u32 ok, x = GX_STEAL_NONE;
+    asm volatile("{\n .reg .b128 r;\n .reg .pred p;\n ld.shared.b128 r, [%1];\n"
+                 " clusterlaunchcontrol.query_cancel.is_canceled.pred.b128 p, r;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(resp)
+                 : "memory");
+    if (ok)
+        asm volatile("{\n .reg .b128 r;\n ld.shared.b128 r, [%1];\n"
+                     " clusterlaunchcontrol.query_cancel.get_first_ctaid::x.b32.b128 %0, r;\n}"
+                     : "=r"(x)
+                     : "r"(resp)
+                     : "memory");
+    return x;
+}
+
+/*
+ * The skeleton of modes 2 and 3: exec_tiles' chunk handling (restaging on a program
  * change, the combining area kept open across a program's consecutive chunks) driven by
- * steal_walk.  Every callback's result is taken by thread 0 (the hook's by warp 0, with
- * lane 0 the only valid lane) and handed to the block through shared memory between two
- * barriers, so every thread takes the same path.  `hook(env, ctxw, valid, idx)` runs the
- * scheduling program's per-event code on a transposed one-record tile.
+ * one of two walks.
+ *   mode 2 (persistent, one share per block): steal_walk.
+ *   mode 3 (one block per chunk, cluster launch control): block b runs chunk b; then,
+ *     while chunks have not all started and the hook says yes, it cancels a block that
+ *     has not launched and runs that block's chunk.  A cancelled block never runs, and
+ *     each is handed to one canceller, so every chunk runs once.  The first failed
+ *     cancel ends the block's stealing.
+ * Every callback's result is taken by thread 0 (the hook's by warp 0, with lane 0 the
+ * only valid lane) and handed to the block through shared memory between two barriers,
+ * so every thread takes the same path.  `hook(env, ctxw, valid, idx)` runs the scheduling
+ * program's per-event code on a transposed one-record tile.
  */
 template <typename RunChunk, typename Init, typename Flush, typename Hook>
 __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chunk, Init wc_init, Flush wc_flush,
@@ -128,11 +210,20 @@ __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chu
     __shared__ u32 s_word;
     __shared__ const uint8_t *s_image;
     __shared__ u64 s_hctx[GX_SCHED_CTX / 8 * GX_CTX_ROW(GX_SCHED_CTX / 8)];
+    __shared__ __align__(16) uint4 s_resp;  /* mode 3: the cancel response */
+    __shared__ __align__(8) u64 s_mbar;     /* mode 3: its completion barrier */
     const gx_steal_hdr *H = (const gx_steal_hdr *)P.cursor;
     const u32 n = H->nchunks, shares = H->shares, self = blockIdx.x;
     const u32 row = GX_CTX_ROW(GX_SCHED_CTX / 8);
     u64 *ctx_all = (u64 *)(smem + P.image_area);
-    if (threadIdx.x == 0) s_image = nullptr;
+    const u32 resp = (u32)__cvta_generic_to_shared(&s_resp), mbar = (u32)__cvta_generic_to_shared(&s_mbar);
+    if (threadIdx.x == 0) {
+        s_image = nullptr;
+        if (P.mode == 3) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     for (u32 i = threadIdx.x; i < GX_SCHED_CTX / 8 * row; i += blockDim.x) s_hctx[i] = 0;
     const u64 t0 = steal_now_ns();
     ExecEnv open;
@@ -173,6 +264,7 @@ __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chu
         return s_word != 0;
     };
     auto run = [&](u32 c) {
+        if (P.mode == 3 && threadIdx.x == 0) atomicAdd(&H->next[0], 1u);
         const gx_chunk ch = P.chunks[c];
         const u32 wcp = (ch.pad >> 63) ? (u32)(ch.pad >> 32) & 0x1FFu : P.wc_bits; /* the chunk's own choice */
         if (is_open && ((u32)ch.pad != open.slot || wcp != open_wcp)) {
@@ -194,7 +286,29 @@ __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chu
         }
         run_chunk(env, ch, ctx_all);
     };
-    steal_walk(self, shares, n, claim, left, ask, run, t);
+    if (P.mode != 3) {
+        steal_walk(self, shares, n, claim, left, ask, run, t);
+    } else {
+        __syncthreads(); /* the barrier's initialisation */
+        u32 phase = 0;
+        auto cancel = [&]() -> u32 {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_word = steal_cancel_one(resp, mbar, phase);
+                if (s_word == GX_STEAL_STUCK) { /* the response never came: stop, and say so */
+                    const ExecEnv he = stage_env_at((uint8_t *)H->hook, 0, 0, 0);
+                    atomicAdd(&he.stats[GX_STAT_WAITS], 1ull);
+                    set_status(he.stats, GX_E_TIMEOUT);
+                }
+            }
+            __syncthreads();
+            phase ^= 1u;
+            return s_word;
+        };
+        cancel_walk(
+            self, n, [&]() -> u32 { return left(0, n); },
+            [&](u32 l, u32 done) -> bool { return ask(0, l, done); }, cancel, run, t);
+    }
     __syncthreads();
     if (is_open) wc_flush(open);
     if (threadIdx.x == 0)

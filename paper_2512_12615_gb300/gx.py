@@ -73,6 +73,7 @@ SCHED_OFF_BLOCK, SCHED_OFF_SM, SCHED_OFF_DONE, SCHED_OFF_LEFT, SCHED_OFF_ELAPSED
 SCHED_MAX_INSNS, SCHED_MAX_HELPERS, SCHED_MAX_MEM = 64, 2, 16
 STEAL_OWNED, STEAL_STOLEN, STEAL_ASKED, STEAL_GRANTED = range(4)
 STEAL_WORDS = 4
+SCHED_F_LAUNCH_CONTROL = 1
 
 
 SHARDS_OFF = 255
@@ -157,8 +158,8 @@ _SIGS = {
     "gx_batch_plan": (i32, [ctypes.c_void_p, ctypes.POINTER(Launch), ctypes.c_void_p]),
     "gx_batch_launch": (i32, [ctypes.c_void_p, ctypes.c_void_p]),
     "gx_batch_destroy": (i32, [ctypes.c_void_p]),
-    "gx_batch_set_sched": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(SimtSpec), ctypes.c_char_p,
-                                 ctypes.c_size_t]),
+    "gx_batch_set_sched": (i32, [ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.POINTER(SimtSpec), u32,
+                                 ctypes.c_char_p, ctypes.c_size_t]),
     "gx_batch_sched_tally": (i32, [ctypes.c_void_p, ctypes.c_void_p, u32, ctypes.POINTER(u32), ctypes.c_void_p]),
     "gx_server_create": (i32, [ctypes.c_void_p, ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)]),
     "gx_server_submit": (i32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, u64, ctypes.c_void_p, u64, dbl]),
@@ -510,13 +511,15 @@ class Batch:
     def launch(self, stream=None) -> None:
         check(lib().gx_batch_launch(self.h, _stream(stream)), "gx_batch_launch")
 
-    def set_sched(self, hook: Program, budget_ns: int = 0, *, max_insns: Optional[int] = None,
-                  max_helper_calls: Optional[int] = None, max_mem_ops: Optional[int] = None) -> None:
-        """Steer the blocks with a scheduling program (gx_batch_set_sched); before plan()."""
+    def set_sched(self, hook: Program, budget_ns: int = 0, *, launch_control: bool = False,
+                  max_insns: Optional[int] = None, max_helper_calls: Optional[int] = None,
+                  max_mem_ops: Optional[int] = None) -> None:
+        """Steer the blocks with a scheduling program (gx_batch_set_sched); before plan().
+        launch_control: one block per chunk, stealing by cancelling blocks not yet started."""
         lim = _sched_limits(max_insns, max_helper_calls, max_mem_ops)
         log = ctypes.create_string_buffer(1 << 16)
-        rc = lib().gx_batch_set_sched(self.h, hook.h, budget_ns, None if lim is None else ctypes.byref(lim), log,
-                                      1 << 16)
+        rc = lib().gx_batch_set_sched(self.h, hook.h, budget_ns, None if lim is None else ctypes.byref(lim),
+                                      SCHED_F_LAUNCH_CONTROL if launch_control else 0, log, 1 << 16)
         check(rc, "gx_batch_set_sched: " + log.value.decode())
         self._sched = hook
 

@@ -8,13 +8,17 @@
  *   - a policy that never steals leaves each block exactly its own share;
  *   - the counters agree: asked >= granted >= stolen, owned + stolen summed = chunks;
  *   - every walk ends, within its own share + one failed claim per share of claims.
+ * The same for the walk of one block per chunk (cancel_walk) over a model of the launcher:
+ * a cancelled block never starts, and no block cancels again after a failed cancel.
  * Prints OK or the failed checks.
  */
 #include "gx_steal.cuh" /* compiled with the engine's csrc/ (or a mutant copy) on the include path */
 
 #include <atomic>
 #include <cstdio>
+#include <deque>
 #include <memory>
+#include <mutex>
 #include <random>
 #include <thread>
 #include <vector>
@@ -95,6 +99,109 @@ struct Run {
     }
 };
 
+/*
+ * Mode 3: one block per chunk.  The launcher model keeps the blocks not yet started in a
+ * queue; idle workers (the SMs) launch the next one, and a cancel takes one out of the
+ * queue (the last, as a scheduler that launches in order would have started the others
+ * first), so a cancelled block never runs.
+ */
+struct Launch {
+    uint32_t n, grid;
+    std::mutex mu;
+    std::deque<uint32_t> pending;
+    std::vector<uint8_t> cancelled;
+    std::atomic<uint32_t> started{0};
+    std::unique_ptr<std::atomic<uint32_t>[]> runs;
+    std::vector<uint32_t> t;
+    explicit Launch(uint32_t n_)
+        : n(n_), grid(n_ ? n_ : 1), cancelled(grid, 0), runs(new std::atomic<uint32_t>[grid]), t(grid * GX_STEAL_WORDS, 0) {
+        for (uint32_t b = 0; b < grid; b++) {
+            pending.push_back(b);
+            runs[b] = 0;
+        }
+    }
+    uint32_t launch_next() {
+        std::lock_guard<std::mutex> g(mu);
+        if (pending.empty()) return ~0u;
+        const uint32_t b = pending.front();
+        pending.pop_front();
+        return b;
+    }
+    uint32_t cancel_one() {
+        std::lock_guard<std::mutex> g(mu);
+        if (pending.empty()) return ~0u;
+        const uint32_t b = pending.back();
+        pending.pop_back();
+        cancelled[b] = 1;
+        return b;
+    }
+    void walk(uint32_t self, Policy pol, uint64_t seed, bool yield) {
+        std::mt19937_64 rng(seed);
+        uint32_t *tt = &t[self * GX_STEAL_WORDS];
+        bool failed = false;
+        auto left = [&]() {
+            const uint32_t k = started.load();
+            return k < n ? n - k : 0u;
+        };
+        auto ask = [&](uint32_t l, uint32_t done) {
+            CHECK(l > 0);
+            CHECK(done == tt[GX_STEAL_OWNED] + tt[GX_STEAL_STOLEN]);
+            if (tt[GX_STEAL_ASKED] > n + 64) { /* a walk that keeps asking */
+                CHECK(!"the walk does not end");
+                return false;
+            }
+            switch (pol) {
+            case NEVER: return false;
+            case ALWAYS: return true;
+            case RANDOM: return (rng() & 1) != 0;
+            case FIRST_K: return tt[GX_STEAL_ASKED] <= 3;
+            }
+            return false;
+        };
+        auto cancel = [&]() {
+            CHECK(!failed); /* a cancel after a failed one */
+            if (yield && (rng() & 3) == 0) std::this_thread::yield();
+            const uint32_t c = cancel_one();
+            failed = c >= n;
+            return c;
+        };
+        auto run = [&](uint32_t c) {
+            CHECK(c < n);
+            if (c >= n) return;
+            CHECK(c == self || cancelled[c]);
+            started.fetch_add(1);
+            runs[c].fetch_add(1);
+        };
+        CHECK(!cancelled[self]); /* a cancelled block never starts */
+        gx::cancel_walk(self, n, left, ask, cancel, run, tt);
+    }
+    void check_common(Policy pol) {
+        uint64_t done = 0;
+        for (uint32_t c = 0; c < n; c++) CHECK(runs[c].load() == 1);
+        for (uint32_t b = 0; b < grid; b++) {
+            const uint32_t *tt = &t[b * GX_STEAL_WORDS];
+            done += tt[GX_STEAL_OWNED] + tt[GX_STEAL_STOLEN];
+            CHECK(tt[GX_STEAL_OWNED] == (cancelled[b] || b >= n ? 0u : 1u));
+            if (cancelled[b]) CHECK(tt[GX_STEAL_ASKED] == 0);
+            CHECK(tt[GX_STEAL_ASKED] >= tt[GX_STEAL_GRANTED] && tt[GX_STEAL_GRANTED] >= tt[GX_STEAL_STOLEN]);
+            CHECK(tt[GX_STEAL_GRANTED] - tt[GX_STEAL_STOLEN] <= 1); /* one failed cancel ends the walk */
+            if (pol == NEVER) CHECK(tt[GX_STEAL_STOLEN] == 0 && tt[GX_STEAL_ASKED] <= 1);
+        }
+        CHECK(done == n);
+    }
+};
+
+static void launched(uint32_t n, uint32_t workers, Policy pol, uint64_t seed) {
+    Launch L(n);
+    std::vector<std::thread> th;
+    for (uint32_t w = 0; w < workers; w++)
+        th.emplace_back([&L, w, pol, seed] {
+            for (uint32_t b; (b = L.launch_next()) != ~0u;) L.walk(b, pol, seed * 7919u + w * 131u + b, true);
+        });
+    for (auto &x : th) x.join();
+    L.check_common(pol);
+}
+
 /* blocks as threads, interleaved by the OS (and random yields) */
 static void threaded(uint32_t n, uint32_t shares, Policy pol, uint64_t seed) {
     Run r(n, shares);
@@ -162,6 +269,34 @@ int main() {
         for (uint32_t b = 0; b < 8; b++) r1.walk(b, ALWAYS, 5, false);
         r1.check_common(ALWAYS);
     }
+
+    /* mode 3, one worker: block 0 runs its chunk, then cancels every other block and runs its chunk */
+    {
+        Launch L(10);
+        for (uint32_t b; (b = L.launch_next()) != ~0u;) L.walk(b, ALWAYS, 6, false);
+        L.check_common(ALWAYS);
+        CHECK(L.t[GX_STEAL_OWNED] == 1 && L.t[GX_STEAL_STOLEN] == 9 && L.t[GX_STEAL_ASKED] == 9);
+    }
+    {
+        /* a block launched but not yet started keeps `left` above zero; the cancel that finds
+           no block waiting ends the walk (a second cancel would be an error) */
+        Launch L(6);
+        const uint32_t first = L.launch_next(), second = L.launch_next(); /* blocks 0 and 1 launched */
+        CHECK(first == 0 && second == 1);
+        L.walk(0, ALWAYS, 7, false); /* cancels 5, 4, 3, 2; then block 1 has not started */
+        CHECK(L.t[GX_STEAL_STOLEN] == 4 && L.t[GX_STEAL_GRANTED] == 5 && L.t[GX_STEAL_ASKED] == 5);
+        L.walk(1, ALWAYS, 8, false);
+        L.check_common(ALWAYS);
+    }
+    {
+        Launch L(0); /* an empty table still launches one block, which does nothing */
+        L.walk(L.launch_next(), ALWAYS, 9, false);
+        L.check_common(ALWAYS);
+        CHECK(L.t[GX_STEAL_ASKED] == 0);
+    }
+    for (Policy pol : {NEVER, ALWAYS, RANDOM, FIRST_K})
+        for (uint32_t n : {0u, 1u, 7u, 300u, 3000u})
+            for (uint32_t w : {1u, 4u, 16u}) launched(n, w, pol, n * 31u + w);
 
     /* interleaved: every policy, sizes around the share count */
     uint64_t seed = 11;

@@ -12,10 +12,13 @@ they hold it to:
   - the scheduling program's own statistics map counts exactly the asks and grants the
     tallies report (its decisions are per-SM-group counts, Sec. 6's policies as written);
   - the refusals: a scheduling program that is interpreted, warp-level, of another context
-    size or over the hook budget; a batch with an interpreted item.
+    size or over the hook budget; a batch with an interpreted item;
+  - the same with one block per chunk and cluster launch control (launch_control=True):
+    cancelled blocks leave zero rows, every other block ran its own chunk.
 The walk itself (exactly-once under any interleaving) is pinned on the host
 (tests/test_host_steal.py); the kernel compiles on the host (tests/test_jit_compile.py).
-Run `-k first_run` alone first: one small item, FixedWork.
+Run `-k first_run` alone first: one small item, FixedWork (then Greedy under launch control,
+the first run of its cancel and bounded mbarrier wait).
 """
 import numpy as np
 import pytest
@@ -66,12 +69,12 @@ def share_sizes(nchunks, shares):
     return np.diff(np.array(lo, dtype=np.int64))
 
 
-def run_sched(ctx, items, kind, budget_ns, shape, launches=1):
+def run_sched(ctx, items, kind, budget_ns, shape, launches=1, launch_control=False):
     hp, hm = hook_program(ctx, kind)
     b = gx.Batch(ctx)
     for it in items:
         b.add(it["gp"], it["dev"], len(it["ev"]), it["ret"])
-    b.set_sched(hp, budget_ns)
+    b.set_sched(hp, budget_ns, launch_control=launch_control)
     b.plan(launch=shape)
     tallies = []
     for _ in range(launches):
@@ -130,6 +133,48 @@ def test_policies_match_oracle(ctx, kind, budget_ns, shape):
     for t in tallies:
         check_tally(t, nchunks, never)
     # the scheduling program counted every ask and every grant of both launches
+    assert int(stats[:, 0].sum()) == int(sum(t[:, gx.STEAL_ASKED].sum() for t in tallies))
+    assert int(stats[:, 1].sum()) == int(sum(t[:, gx.STEAL_GRANTED].sum() for t in tallies))
+
+
+def check_tally_lc(t, nchunks, never_steals):
+    """One block per chunk: rows of cancelled blocks are zero, every other block ran its own
+    chunk, and one failed cancel at most ends each walk."""
+    own, stolen, asked, granted = (t[:, k].astype(np.int64) for k in range(gx.STEAL_WORDS))
+    assert len(t) == max(nchunks, 1)
+    assert int(own.sum() + stolen.sum()) == nchunks
+    assert set(own.tolist()) <= {0, 1}
+    assert (asked >= granted).all() and (granted >= stolen).all() and (granted - stolen <= 1).all()
+    assert int(own.sum()) == nchunks - int(stolen.sum())  # a block is cancelled or runs its own chunk
+    if never_steals:
+        assert (own == 1).all() and stolen.sum() == 0 and granted.sum() == 0
+
+
+def test_first_run_launch_control_small(ctx):
+    """Cluster launch control, smallest case: 5 chunks, one block each, FixedWork (no cancel
+    is ever issued).  Then Greedy on the same sizes, where blocks may cancel."""
+    items = make_items(ctx, [0], [5000], seed=110)
+    (t,), stats, status = run_sched(ctx, items, "fixed", 0, (256, 4), launch_control=True)
+    assert status == 0
+    check_items(items, 1)
+    check_tally_lc(t, 5, never_steals=True)
+    items = make_items(ctx, [0], [5000], seed=111)
+    (t,), stats, status = run_sched(ctx, items, "greedy", 0, (256, 4), launch_control=True)
+    assert status == 0
+    check_items(items, 1)
+    check_tally_lc(t, 5, never_steals=False)
+    assert int(stats[:, 1].sum()) == int(t[:, gx.STEAL_GRANTED].sum())
+
+
+@pytest.mark.parametrize("kind,budget_ns", [("fixed", 0), ("greedy", 0), ("latency_budget", 10**12)])
+def test_launch_control_matches_oracle(ctx, kind, budget_ns):
+    items = make_items(ctx, PICK, SIZES, seed=500)
+    tallies, stats, status = run_sched(ctx, items, kind, budget_ns, (256, 4), launches=2, launch_control=True)
+    assert status == 0
+    check_items(items, 2)
+    nchunks = sum((n + 1023) // 1024 for n in SIZES)
+    for t in tallies:
+        check_tally_lc(t, nchunks, kind == "fixed")
     assert int(stats[:, 0].sum()) == int(sum(t[:, gx.STEAL_ASKED].sum() for t in tallies))
     assert int(stats[:, 1].sum()) == int(sum(t[:, gx.STEAL_GRANTED].sum() for t in tallies))
 

@@ -2,7 +2,9 @@
 the shares cut the chunk table exactly; whatever a `should_try_steal` policy answers and
 however blocks interleave (host threads claiming with atomic adds), every chunk runs once,
 a policy that never steals leaves each block its own share, the per-block counters agree
-and every walk ends within its claim bound; plus exact pins for blocks walked in turn.
+and every walk ends within its claim bound; plus exact pins for blocks walked in turn.  The
+walk of one block per chunk (cancel_walk) runs over a model of the launcher: a cancelled
+block never starts and no block cancels again after a failed cancel.
 The same check run over planted mistakes in a copy of the walk must fail.  No device is
 touched."""
 import os
@@ -48,6 +50,13 @@ MUTANTS = {
                                        "if (!ask(v, l, t[GX_STEAL_OWNED] + t[GX_STEAL_STOLEN])) break;"),
     "the owner never drains": ("    for (;;) {\n        const uint32_t k = claim(self);",
                                "    for (int once_ = 0; once_ < 1; once_++) {\n        const uint32_t k = claim(self);"),
+    # one block per chunk (cancel_walk)
+    "cancels again after a failed cancel": ("const uint32_t c = cancel();\n        if (c >= n) break;",
+                                            "const uint32_t c = cancel();\n        if (c >= n) continue;"),
+    "asks with nothing left": ("const uint32_t l = left();\n        if (l == 0) break;",
+                               "const uint32_t l = left();"),
+    "runs its own chunk again for a cancelled one": ("if (c >= n) break;\n        run(c);",
+                                                      "if (c >= n) break;\n        run(self);"),
 }
 
 
