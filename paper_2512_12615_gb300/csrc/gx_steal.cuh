@@ -32,7 +32,7 @@
 #define GX_STEAL_FN inline
 #endif
 
-/* ExecParams.mode 2: ExecParams.cursor points at this header (the persistent header block) */
+/* ExecParams.mode 2 and 3: ExecParams.cursor points at this header (the persistent header block) */
 typedef struct gx_steal_hdr {
     uint32_t unused;        /* the claim cursor of mode 1 */
     uint32_t nchunks;       /* chunks in the table (where mode 1 keeps its count) */
@@ -299,6 +299,8 @@ __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chu
                     const ExecEnv he = stage_env_at((uint8_t *)H->hook, 0, 0, 0);
                     atomicAdd(&he.stats[GX_STAT_WAITS], 1ull);
                     set_status(he.stats, GX_E_TIMEOUT);
+                    /* once more, bounded: the response is still owed to this block's shared memory */
+                    steal_mbar_wait(mbar, phase);
                 }
             }
             __syncthreads();
