@@ -381,6 +381,69 @@ def run_batched(gx, torch):
     return out
 
 
+def run_sched(gx, torch):
+    """The 64-program batch under each `should_try_steal` policy (FixedWork, Greedy, LatencyBudget;
+    Sec. 6), with persistent shares and with cluster launch control, beside the claim-cursor
+    batch at the same launch shape.  LatencyBudget's budget is half of FixedWork's time."""
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+    sizes = P.batch_sizes()
+    ctx = gx.Context(torch.cuda.current_device())
+    items = build_batch(gx, torch, ctx, sizes)
+    total = sum(sizes)
+    shape = (256, 4)
+
+    def timed(b):
+        for _ in range(2):
+            b.launch(stream=sid)
+        ts = []
+        for _ in range(5):
+            t = EventTimer(stream)
+            with t:
+                b.launch(stream=sid)
+            ts.append(t.ms())
+        return float(np.median(ts))
+
+    out = {"workload": f"64 generated programs over log-uniform batches 4K-16M, {total} events",
+           "launch": {"block": shape[0], "ept": shape[1]}}
+    b = gx.Batch(ctx)
+    for prog, _, dev, n in items:
+        b.add(prog, dev, n)
+    b.plan(launch=shape, stream=sid)
+    ms = timed(b)
+    out["claim_cursor"] = {"ms": round(ms, 3), "Mevents_per_s": round(total / ms / 1e3, 1)}
+    b.destroy()
+    for lc in (False, True):
+        budget_ns = 0
+        for kind in ("fixed", "greedy", "latency_budget"):
+            hook, hspecs, cs = P.sched_policy(kind)
+            hm = [gx.Map.from_spec(ctx, s) for s in hspecs]
+            hp = gx.Program(ctx, hook, hm, cs, jit=True)
+            b = gx.Batch(ctx)
+            for prog, _, dev, n in items:
+                b.add(prog, dev, n)
+            b.set_sched(hp, budget_ns, launch_control=lc)
+            b.plan(launch=shape, stream=sid)
+            ms = timed(b)
+            tally = b.sched_tally(stream=sid)
+            if kind == "fixed":
+                budget_ns = int(ms * 1e6 / 2)
+            out[("launch_control_" if lc else "shares_") + kind] = {
+                "ms": round(ms, 3), "Mevents_per_s": round(total / ms / 1e3, 1), "blocks": int(len(tally)),
+                "stolen": int(tally[:, gx.STEAL_STOLEN].sum()), "asked": int(tally[:, gx.STEAL_ASKED].sum()),
+                "budget_ns": budget_ns if kind == "latency_budget" else None, "status": int(hp.status().status)}
+            b.destroy()
+            hp.destroy()
+            for m in hm:
+                m.destroy()
+    for prog, maps, dev, n in items:
+        prog.destroy()
+        for m in maps:
+            m.destroy()
+    ctx.close()
+    return out
+
+
 def run_served(gx, torch, seconds: float, lam: float = 20000.0):
     ctx = gx.Context(torch.cuda.current_device())
     rng = np.random.default_rng(SEED)
@@ -510,8 +573,9 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "headline", "latency", "batched", "served"],
-                    help="all / the headline line only / one config alone (for profiling)")
+    ap.add_argument("--only", default="all", choices=["all", "headline", "latency", "batched", "served", "sched"],
+                    help="all / the headline line only / one config alone (for profiling); sched: the "
+                         "64-program batch under each scheduling policy (not part of the default line)")
     ap.add_argument("--pairs", type=int, default=C3_PAIRS, help="latency pairs with --only latency")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="served config arrival rate (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -534,9 +598,10 @@ def main() -> int:
     import paper_2512_12615_gb300 as gx
 
     gx.lib()
-    if args.only in ("latency", "batched", "served"):
+    if args.only in ("latency", "batched", "served", "sched"):
         one = {"latency": lambda: run_latency(gx, torch, True, args.pairs), "batched": lambda: run_batched(gx, torch),
-               "served": lambda: run_served(gx, torch, args.serve_seconds, args.serve_rate)}[args.only]()
+               "served": lambda: run_served(gx, torch, args.serve_seconds, args.serve_rate),
+               "sched": lambda: run_sched(gx, torch)}[args.only]()
         if rank == 0:
             print(json.dumps({"config": args.only, **one}), flush=True)
         return 0
