@@ -444,6 +444,47 @@ def run_sched(gx, torch):
     return out
 
 
+def run_warp(gx, torch, steps: int, warmup: int, n_warps: int = 1 << 21):
+    """warp_heat over warp-context records (the warp-level form: one handler per warp, the leader's
+    side effects once), page-heat beside it at the same record count and launch shape.  Both read
+    32 B per record; roofline against the measured copy bandwidth."""
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+    n = n_warps * 32
+    ctx = gx.Context(torch.cuda.current_device())
+    shape = (256, 8)
+    out = {"workload": f"{n_warps} warps x 32 lanes of warp-context records (75% coalesced, Zipf(1.1) pages)",
+           "events": n, "launch": {"block": shape[0], "ept": shape[1]}, "l2": "inputs 2 GiB per step > 129 MB L2"}
+    peak, peak_kind = peaks()
+    ev = gen.warp_access_events(n_warps)
+    dev = to_device(ev)
+    for name, build, simt in (("warp_heat", P.warp_heat, {"uniform": gen.WARP_UNIFORM}),
+                              ("page_heat", P.page_heat, None)):
+        prog_i, specs, cs = build()
+        maps = [gx.Map.from_spec(ctx, sp) for sp in specs]
+        prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=True, simt=simt)
+        for _ in range(max(3, warmup)):
+            prog.run(dev, n, launch=shape, stream=sid)
+        ts = []
+        for _ in range(max(1, steps)):
+            t = EventTimer(stream)
+            with t:
+                prog.run(dev, n, launch=shape, stream=sid)
+            ts.append(t.ms())
+        st = prog.status()
+        ms = float(np.median(ts))
+        achieved = n * 32 / (ms / 1e3) / 1e9
+        out[name] = {"ms": round(ms, 4), "Mevents_per_s": round(n / ms / 1e3, 1), "status": int(st.status),
+                     "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                  "frac": round(achieved / peak, 4), "peak_kind": peak_kind}}
+        prog.destroy()
+        for m in maps:
+            m.destroy()
+    del dev
+    ctx.close()
+    return out
+
+
 def run_served(gx, torch, seconds: float, lam: float = 20000.0):
     ctx = gx.Context(torch.cuda.current_device())
     rng = np.random.default_rng(SEED)
@@ -573,9 +614,11 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "headline", "latency", "batched", "served", "sched"],
+    ap.add_argument("--only", default="all", choices=["all", "headline", "latency", "batched", "served", "sched",
+                                                      "warp"],
                     help="all / the headline line only / one config alone (for profiling); sched: the "
-                         "64-program batch under each scheduling policy (not part of the default line)")
+                         "64-program batch under each scheduling policy; warp: warp_heat's warp-level form "
+                         "beside page-heat (neither part of the default line)")
     ap.add_argument("--pairs", type=int, default=C3_PAIRS, help="latency pairs with --only latency")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="served config arrival rate (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -598,10 +641,11 @@ def main() -> int:
     import paper_2512_12615_gb300 as gx
 
     gx.lib()
-    if args.only in ("latency", "batched", "served", "sched"):
+    if args.only in ("latency", "batched", "served", "sched", "warp"):
         one = {"latency": lambda: run_latency(gx, torch, True, args.pairs), "batched": lambda: run_batched(gx, torch),
                "served": lambda: run_served(gx, torch, args.serve_seconds, args.serve_rate),
-               "sched": lambda: run_sched(gx, torch)}[args.only]()
+               "sched": lambda: run_sched(gx, torch),
+               "warp": lambda: run_warp(gx, torch, args.steps, args.warmup)}[args.only]()
         if rank == 0:
             print(json.dumps({"config": args.only, **one}), flush=True)
         return 0
