@@ -61,15 +61,22 @@ GX_STEAL_FN uint32_t share_lo(uint32_t s, uint32_t shares, uint32_t n) {
     return (uint32_t)((uint64_t)s * n / shares);
 }
 
+/* the share `o` places after share `self` (cyclically) */
+GX_STEAL_FN uint32_t share_after(uint32_t self, uint32_t o, uint32_t shares) {
+    return self + o < shares ? self + o : self + o - shares;
+}
+
 /*
  * One block's walk over the shares.  claim(s): the share's next offset (one atomic add);
  * left(s, size): chunks of share s not yet handed out (an advisory read, possibly stale);
- * ask(s, left, done): the hook's answer; run(c): run chunk c.  t[GX_STEAL_*] counts what
- * the block did.
+ * find(after): the smallest o in (after, shares) whose share share_after(self, o) showed
+ * chunks left, else `shares` (advisory too); ask(s, left, done): the hook's answer;
+ * run(c): run chunk c.  t[GX_STEAL_*] counts what the block did.  The other shares are
+ * visited once each, in order after the block's own.
  */
-template <class Claim, class Left, class Ask, class Run>
-GX_STEAL_FN void steal_walk(uint32_t self, uint32_t shares, uint32_t n, Claim claim, Left left, Ask ask, Run run,
-                            uint32_t *t) {
+template <class Claim, class Left, class Find, class Ask, class Run>
+GX_STEAL_FN void steal_walk(uint32_t self, uint32_t shares, uint32_t n, Claim claim, Left left, Find find, Ask ask,
+                            Run run, uint32_t *t) {
     uint32_t lo = share_lo(self, shares, n), size = share_lo(self + 1, shares, n) - lo;
     for (;;) {
         const uint32_t k = claim(self);
@@ -77,8 +84,8 @@ GX_STEAL_FN void steal_walk(uint32_t self, uint32_t shares, uint32_t n, Claim cl
         run(lo + k);
         t[GX_STEAL_OWNED]++;
     }
-    for (uint32_t i = 1; i < shares; i++) {
-        const uint32_t v = self + i < shares ? self + i : self + i - shares;
+    for (uint32_t o = find(0u); o < shares; o = find(o)) {
+        const uint32_t v = share_after(self, o, shares);
         lo = share_lo(v, shares, n);
         size = share_lo(v + 1, shares, n) - lo;
         for (;;) {
@@ -245,6 +252,26 @@ __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chu
         __syncthreads();
         return s_word;
     };
+    /* block-parallel: each thread reads one share's counter per step, __syncthreads_or decides */
+    auto find = [&](u32 after) -> u32 {
+        __syncthreads();
+        if (threadIdx.x == 0) s_word = shares;
+        for (u32 o0 = after + 1; o0 < shares; o0 += blockDim.x) {
+            const u32 o = o0 + threadIdx.x;
+            bool has = false;
+            if (o < shares) {
+                const u32 v = share_after(self, o, shares);
+                const u32 size = share_lo(v + 1, shares, n) - share_lo(v, shares, n);
+                has = *(volatile const u32 *)&H->next[v] < size;
+            }
+            if (__syncthreads_or(has)) {
+                if (has) atomicMin(&s_word, o);
+                __syncthreads();
+                return s_word;
+            }
+        }
+        return shares;
+    };
     auto ask = [&](u32 s, u32 l, u32 done) -> bool {
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -287,7 +314,7 @@ __device__ __forceinline__ void exec_steal(const ExecParams &P, RunChunk run_chu
         run_chunk(env, ch, ctx_all);
     };
     if (P.mode != 3) {
-        steal_walk(self, shares, n, claim, left, ask, run, t);
+        steal_walk(self, shares, n, claim, left, find, ask, run, t);
     } else {
         __syncthreads(); /* the barrier's initialisation */
         u32 phase = 0;

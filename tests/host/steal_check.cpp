@@ -74,7 +74,15 @@ struct Run {
             CHECK(c < n);
             if (c < n) runs[c].fetch_add(1);
         };
-        gx::steal_walk(self, shares, n, claim, left, ask, run, tt);
+        uint32_t last = 0;
+        auto find = [&](uint32_t after) {
+            CHECK(after == last); /* one forward pass over the other shares */
+            for (uint32_t o = after + 1; o < shares; o++)
+                if (next[gx::share_after(self, o, shares)].load() < size(gx::share_after(self, o, shares)))
+                    return last = o;
+            return last = shares;
+        };
+        gx::steal_walk(self, shares, n, claim, left, find, ask, run, tt);
     }
 
     void check_common(Policy pol) {

@@ -50,6 +50,7 @@ MUTANTS = {
                                        "if (!ask(v, l, t[GX_STEAL_OWNED] + t[GX_STEAL_STOLEN])) break;"),
     "the owner never drains": ("    for (;;) {\n        const uint32_t k = claim(self);",
                                "    for (int once_ = 0; once_ < 1; once_++) {\n        const uint32_t k = claim(self);"),
+    "restarts the search from the first share": ("o < shares; o = find(o))", "o < shares; o = find(0u))"),
     # one block per chunk (cancel_walk)
     "cancels again after a failed cancel": ("const uint32_t c = cancel();\n        if (c >= n) break;",
                                             "const uint32_t c = cancel();\n        if (c >= n) continue;"),
