@@ -639,7 +639,7 @@ static int helper(hctx *h, int32_t id, uint64_t *R) {
         if (!src && R[3]) return OR_EFAULT;
         uint8_t tmp[4096];
         if (R[3] > sizeof tmp) return OR_EINVAL;
-        memcpy(tmp, src, R[3]);
+        if (R[3]) memcpy(tmp, src, R[3]); /* a zero-size output may name no memory at all */
         uint8_t *p = rb_reserve(m, R[3], h->event_idx);
         if (!p) {
             r0 = (uint64_t)(int64_t)OR_EAGAIN;

@@ -694,7 +694,7 @@ struct Verifier {
         }
         op_ranges[p.map].push_back(OpRange{lo, hi, cls, size});
         /* the words this update may change, for merging copies (8-byte updates are 8-aligned) */
-        static_assert(OPC_ADD == UC_ADD && OPC_MIN == UC_MIN, "one numbering for update classes");
+        static_assert((int)OPC_ADD == (int)UC_ADD && (int)OPC_MIN == (int)UC_MIN, "one numbering for update classes");
         MapUse &u = out->map_use[p.map];
         /* bitwise operations merge per 4-byte word whatever their width; ADD, MAX and MIN by width */
         const bool wide = size == 8 && (cls == OPC_ADD || cls == OPC_MAX || cls == OPC_MIN);
