@@ -1,10 +1,11 @@
 """Memory safety and defined behaviour of the host code that reads untrusted bytecode.
 
-The verifier and decoder (the engine's csrc/verifier.cpp, csrc/decode.cpp) and the oracle
-(oracle/gx_oracle.c, which claims to be safe on programs nobody verified) are built with
-AddressSanitizer and UndefinedBehaviorSanitizer and run over a corpus: the fuzzers'
-program generators, the workload programs and seeded mutants of all of them (bit flips,
-random words, duplicated and dropped instructions).  A sanitizer report fails the test.
+The verifier and decoder (the engine's csrc/verifier.cpp, csrc/decode.cpp), the load-time
+code generator (csrc/jit.cpp, source generation only) and the oracle (oracle/gx_oracle.c,
+which claims to be safe on programs nobody verified) are built with AddressSanitizer and
+UndefinedBehaviorSanitizer and run over a corpus: the fuzzers' program generators, the
+workload programs and seeded mutants of all of them (bit flips, random words, duplicated
+and dropped instructions).  A sanitizer report fails the test.
 """
 import os
 import shutil
@@ -96,3 +97,32 @@ def test_oracle_under_sanitizers(corpus_file, tmp_path):
     r = subprocess.run([str(exe), str(corpus_file), "8"], capture_output=True, text=True, timeout=600, env=ENV)
     assert r.returncode == 0 and r.stdout.startswith("OK"), (r.stdout[-2000:], r.stderr[-6000:])
     assert "runtime error" not in r.stderr, r.stderr[-6000:]
+
+
+def test_code_generator_under_sanitizers(corpus_file, tmp_path):
+    """Every accepted program as per-lane, multi-program, work-stealing and warp-level source
+    (balanced braces and parentheses), in four parallel parts."""
+    import paper_2512_12615_gb300._build as B
+
+    if not shutil.which("g++"):
+        pytest.skip("no host compiler")
+    B.build()  # writes the embedded device headers the generator links against
+    csrc = os.path.join(ROOT, "paper_2512_12615_gb300", "csrc")
+    exe = tmp_path / "jit_sanitize"
+    _compile(["g++", "-std=c++17"] + SAN + ["-O2", "-I" + os.path.join(ROOT, "include"), "-I" + csrc,
+              "-I" + os.path.join(B.CUDA_HOME, "include"), os.path.join(csrc, "jit.cpp"),
+              os.path.join(csrc, "verifier.cpp"), os.path.join(csrc, "decode.cpp"),
+              os.path.join(B.BUILD, "gx_embed.cpp"), os.path.join(HERE, "host", "jit_sanitize.cpp"), "-o", str(exe),
+              "-L" + os.path.join(B.CUDA_HOME, "lib64"), "-lcudart", "-ldl", "-lpthread",
+              "-Wl,-rpath," + os.path.join(B.CUDA_HOME, "lib64")])
+    procs = [subprocess.Popen([str(exe), str(corpus_file), "0", str(k), "4"], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=ENV) for k in range(4)]
+    totals = {}
+    for p in procs:
+        out, err = p.communicate(timeout=600)
+        assert p.returncode == 0 and out.startswith("OK"), (out[-2000:], err[-6000:])
+        assert "runtime error" not in err, err[-6000:]
+        for kv in out.split()[1:]:
+            k, v = kv.split("=")
+            totals[k] = totals.get(k, 0) + int(v)
+    assert totals["lane"] > 200 and totals["warp"] > 100 and totals["multi"] > 50 and totals["sched"] > 30, totals
