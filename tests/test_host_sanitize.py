@@ -36,6 +36,11 @@ def corpus(seed=77):
         out.append(build())
     out += list(P.batch_programs())
     out += [P.sched_policy(k) for k in ("fixed", "greedy", "latency_budget")]
+    import json
+
+    with open(os.path.join(HERE, "golden", "handworked.json")) as f:
+        for case in json.load(f)["cases"]:  # hand-worked programs: every opcode family, faults included
+            out.append((assemble(case["asm"]).prog(), case.get("maps", []), 8 * len(case["events"][0])))
     for gen, specs, cs, n in ((lambda: V.Gen(rng).program(), V.SPECS, V.CTX, 150),
                               (lambda: D.Gen(rng).program(), D.SPECS, 32, 100),
                               (lambda: C.CGen(rng).program(), D.SPECS, 32, 60),
