@@ -474,6 +474,10 @@ int gx_last_status(gx_prog *prog, gx_run_stats *out, int reset, void *stream);
  * cached per program and size bucket and used by later runs, and its sharding choice is
  * the program's default in batches and served ticks; *best (nullable) gets it.
  * Synchronous; GX_EINVAL for n == 0 or a null events_dev.
+ * With the environment variable GX_TUNE_CACHE naming a directory, each choice is also
+ * written there, one file per program, map specs and options, size bucket, device and
+ * engine build. A later call that finds a valid file uses it without timing anything.
+ * Batch planning's per-program sharding choice is cached the same way.
  */
 int gx_autotune(gx_prog *prog, const void *events_dev, uint64_t n, void *stream, gx_launch *best);
 

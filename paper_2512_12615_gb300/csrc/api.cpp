@@ -17,6 +17,7 @@
 #include "gx_internal.h"
 #include "gx_kernels.h"
 #include "gx_runtime.h"
+#include "tune_cache.h"
 
 using namespace gx;
 
@@ -816,6 +817,58 @@ int gx_last_status(gx_prog *p, gx_run_stats *out, int reset, void *stream) {
     return GX_OK;
 }
 
+static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_t s, gx_launch *best, bool policy_only);
+
+/*
+ * What a cached choice is valid for: the program (its micro-ops, and for a specialised
+ * program its kernel key, which covers the generated source and the device headers), its
+ * maps and options, the device (name and SM count) and this engine build.
+ */
+static uint64_t tune_identity(gx_prog *p) {
+    uint64_t h = tune_fnv(p->uops.data(), p->uops.size() * 8);
+    const uint32_t o[3] = {p->opts.ctx_size, p->opts.deterministic, p->opts.flags};
+    h = tune_fnv(o, sizeof o, h);
+    for (auto *m : p->maps) h = tune_fnv(&m->spec, sizeof m->spec, h);
+    if (p->jit) h = tune_fnv(p->jk.key.data(), p->jk.key.size(), h);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->ctx->device) == cudaSuccess) {
+        h = tune_fnv(prop.name, strnlen(prop.name, sizeof prop.name), h);
+        h = tune_fnv(&prop.multiProcessorCount, sizeof prop.multiProcessorCount, h);
+    } else {
+        cudaGetLastError();
+    }
+    static const char build[] = __DATE__ " " __TIME__;
+    return tune_fnv(build, sizeof build, h);
+}
+
+/* the autotuner behind the on-disk cache (GX_TUNE_CACHE): a stored choice is used as is */
+static int autotune_cached(gx_prog *p, const void *events, uint64_t n, cudaStream_t s, gx_launch *best,
+                           bool policy_only) {
+    if (!p || !events || n == 0) return GX_EINVAL;
+    const char *dir = getenv("GX_TUNE_CACHE");
+    const int bucket = 63 - __builtin_clzll(n | 1);
+    std::string path;
+    if (dir && *dir) {
+        path = tune_cache_path(dir, tune_identity(p), bucket, policy_only);
+        gx_launch l;
+        if (tune_cache_load(path, &l)) {
+            if (!policy_only) p->tuned[bucket] = l;
+            p->pref_shards = l.shards;
+            p->pref_tuned = true;
+            if (best) *best = l;
+            return GX_OK;
+        }
+    }
+    gx_launch chosen{};
+    const int rc = autotune_impl(p, events, n, s, &chosen, policy_only);
+    if (rc == GX_OK && !path.empty()) {
+        mkdir(dir, 0755);
+        tune_cache_store(path, chosen);
+    }
+    if (best) *best = chosen;
+    return rc;
+}
+
 static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_t s, gx_launch *best, bool policy_only) {
     if (!p || (!events && n)) return GX_EINVAL;
     if (n == 0) return GX_EINVAL;
@@ -939,7 +992,7 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
 }
 
 int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_launch *best) {
-    return autotune_impl(p, events, n, (cudaStream_t)stream, best, false);
+    return autotune_cached(p, events, n, (cudaStream_t)stream, best, false);
 }
 
 } /* extern "C" */
@@ -951,6 +1004,6 @@ int tune_shards(gx_prog *p, const void *events, uint64_t n, cudaStream_t s) {
         p->pref_shards = 0;
         return GX_OK;
     }
-    return autotune_impl(p, events, n, s, nullptr, true);
+    return autotune_cached(p, events, n, s, nullptr, true);
 }
 } // namespace gx

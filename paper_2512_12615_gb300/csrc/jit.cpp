@@ -661,10 +661,10 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
 }
 
 std::string fnv_hex(const std::string &s) {
-    uint64_t h = 1469598103934665603ULL;
+    uint64_t h = 0xcbf29ce484222325ULL; /* FNV-1a (64-bit): offset basis, then xor and multiply by the prime */
     for (unsigned char c : s) {
         h ^= c;
-        h *= 1099511628211ULL;
+        h *= 0x100000001b3ULL;
     }
     char b[24];
     snprintf(b, sizeof b, "%016llx", (unsigned long long)h);
