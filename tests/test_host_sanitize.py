@@ -131,3 +131,21 @@ def test_code_generator_under_sanitizers(corpus_file, tmp_path):
             k, v = kv.split("=")
             totals[k] = totals.get(k, 0) + int(v)
     assert totals["lane"] > 200 and totals["warp"] > 100 and totals["multi"] > 50 and totals["sched"] > 30, totals
+
+
+def test_sanitized_oracle_catches_a_planted_bounds_bug(corpus_file, tmp_path):
+    """The harness has teeth: in a copy of the oracle whose region check lets an access run
+    past the end of its region, the same corpus makes AddressSanitizer report."""
+    if not shutil.which("gcc"):
+        pytest.skip("no host compiler")
+    src = open(os.path.join(ROOT, "oracle", "gx_oracle.c")).read()
+    old = "if (a >= b && size <= g->r[i].size && a - b <= g->r[i].size - size) {"
+    assert src.count(old) == 1
+    (tmp_path / "oracle").mkdir()
+    (tmp_path / "tests" / "host").mkdir(parents=True)
+    (tmp_path / "oracle" / "gx_oracle.c").write_text(src.replace(old, "if (a >= b && a - b <= g->r[i].size) {"))
+    shutil.copy(os.path.join(HERE, "host", "oracle_sanitize.c"), tmp_path / "tests" / "host")
+    exe = tmp_path / "oracle_mutant"
+    _compile(["gcc", "-std=c11"] + SAN + [str(tmp_path / "tests" / "host" / "oracle_sanitize.c"), "-o", str(exe)])
+    r = subprocess.run([str(exe), str(corpus_file), "8"], capture_output=True, text=True, timeout=600, env=ENV)
+    assert r.returncode != 0 and "AddressSanitizer" in r.stderr, (r.stdout[-500:], r.stderr[-2000:])
