@@ -226,3 +226,31 @@ def test_refusals(ctx):
         b.plan(launch=(256, 4))
     assert e.value.status == gx.EINVAL
     b.destroy()
+
+
+def test_scheduling_program_ring_records(ctx):
+    """A scheduling program that writes its context's first word (block | SM << 32) to a ring
+    buffer at every ask and steals while chunks are left: one record per ask, each carrying
+    its block index as the event index (the gx_batch_set_sched contract)."""
+    lines = ["mov r6 r1", "ldx8 r7 r6 0", "stx8 r10 -8 r7", "ld_map r1 0", "mov r2 r10", "add r2 -8", "mov r3 8",
+             "mov r4 0", "call ringbuf_output", "ldx4 r0 r6 12", "exit"]
+    ring_spec = [dict(type=gx.MAP_RINGBUF, key_size=0, value_size=0, max_entries=1 << 20)]
+    ring = gpu_maps(ctx, ring_spec)
+    hp = gx.Program(ctx, assemble(lines).prog(), ring, gx.SCHED_CTX, jit=True)
+    items = make_items(ctx, PICK, SIZES, seed=600)
+    b = gx.Batch(ctx)
+    for it in items:
+        b.add(it["gp"], it["dev"], len(it["ev"]), it["ret"])
+    b.set_sched(hp, 0)
+    b.plan(launch=(128, 1))
+    b.launch()
+    t = b.sched_tally()
+    torch.cuda.synchronize()
+    raw, dropped = ring[0].drain()
+    recs = gx.parse_records(raw)
+    assert dropped == 0 and len(recs) == int(t[:, gx.STEAL_ASKED].sum())
+    for idx, payload in recs:
+        word = int.from_bytes(payload, "little")
+        assert idx == (word & 0xFFFFFFFF) < len(t)
+    check_items(items, 1)
+    b.destroy()
