@@ -112,7 +112,7 @@ struct Persist {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     gx::JitKernel *jk = nullptr; /* set: the persistent kernel is a multi-program specialised kernel */
-    /* set: mode 2, blocks own shares of the table and this scheduling program steers stealing */
+    /* set: this scheduling program steers stealing (mode 2: blocks own shares of the table; mode 3 below) */
     gx_prog *sched = nullptr;
     uint64_t sched_budget = 0;
     bool launch_control = false; /* mode 3: one block per chunk, stealing by cancelling blocks not yet started */
@@ -173,7 +173,7 @@ struct Persist {
         rc = dalloc(c, dbytes, &dmem);
         if (rc) return rc;
         if (cudaMemset(dmem, 0, 256) != cudaSuccess) return GX_E_CUDA;
-        if (sched) { /* the header of mode 2; the chunk count is written with the table */
+        if (sched) { /* the header of modes 2 and 3; the chunk count is written with the table */
             gx_steal_hdr h;
             memset(&h, 0, sizeof h);
             h.shares = grid;
