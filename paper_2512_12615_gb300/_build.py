@@ -28,7 +28,8 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + os.pa
 
 CU_SOURCES = ["interp.cu"]
 CXX_SOURCES = ["verifier.cpp", "decode.cpp", "api.cpp", "batch.cpp", "jit.cpp"]
-HEADERS = ["gx_layout.h", "gx_internal.h", "gx_kernels.h", "gx_runtime.h", "gx_device.cuh", "gx_jit.h", "gx_steal.cuh", "tune_cache.h"]
+HEADERS = ["gx_layout.h", "gx_internal.h", "gx_kernels.h", "gx_runtime.h", "gx_device.cuh", "gx_jit.h", "gx_steal.cuh", "tune_cache.h",
+           "gx_trace.h"]
 
 
 def _stamp() -> str:

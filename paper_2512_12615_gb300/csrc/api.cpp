@@ -17,6 +17,7 @@
 #include "gx_internal.h"
 #include "gx_kernels.h"
 #include "gx_runtime.h"
+#include "gx_trace.h"
 #include "tune_cache.h"
 
 using namespace gx;
@@ -730,6 +731,7 @@ uint32_t gx_prog_uops(const gx_prog *p) { return p ? (uint32_t)p->uops.size() : 
 /* ---------------------------------------------------------------- runs */
 int gx_run_batch_ex(gx_prog *p, const void *events, uint64_t n, uint64_t idx_base, int64_t *ret_out,
                     const gx_launch *lp, void *stream) {
+    TraceRange tr("gx_run_batch");
     if (!p || (!events && n)) return GX_EINVAL;
     if (((uintptr_t)events) & 15) return GX_EINVAL;
     if (n == 0) return GX_OK;
@@ -745,6 +747,7 @@ int gx_run_batch(gx_prog *p, const void *events, uint64_t n, void *stream) {
 }
 
 int gx_run_batch_host(gx_prog *p, const void *events_host, uint64_t n, int64_t *ret_out_host) {
+    TraceRange tr("gx_run_batch_host");
     if (!p || (!events_host && n)) return GX_EINVAL;
     if (n == 0) return GX_OK;
     const uint64_t cs = p->opts.ctx_size;
@@ -992,6 +995,7 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
 }
 
 int gx_autotune(gx_prog *p, const void *events, uint64_t n, void *stream, gx_launch *best) {
+    TraceRange tr("gx_autotune");
     return autotune_cached(p, events, n, (cudaStream_t)stream, best, false);
 }
 

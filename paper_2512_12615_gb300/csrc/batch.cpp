@@ -35,6 +35,7 @@
 #include "gx_kernels.h"
 #include "gx_runtime.h"
 #include "gx_steal.cuh"
+#include "gx_trace.h"
 
 using namespace gx;
 
@@ -432,6 +433,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
 
 int gx_batch_launch(gx_batch *b, void *stream) {
     if (!b || !b->planned) return GX_EINVAL;
+    TraceRange tr("gx_batch_launch");
     int rc = b->persist.launch((cudaStream_t)stream);
     if (rc == GX_OK) {
         for (auto &it : b->items) it.prog->launches++;
@@ -724,7 +726,10 @@ void gx_server::run() {
                     cudaMemcpyAsync(sl.persist.nchunks(), count, 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
                     rc = GX_E_CUDA;
             }
-            if (rc == GX_OK) rc = sl.persist.launch(sl.stream);
+            if (rc == GX_OK) {
+                TraceRange tr("gx_server_tick");
+                rc = sl.persist.launch(sl.stream);
+            }
             for (auto &r : take) r.prog->launches++;
         }
         if (rc == GX_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = GX_E_CUDA;
