@@ -744,7 +744,9 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
         return "chunk_tiles(env, ch, ctx_all, [](const ExecEnv &e, const u64 *c, bool v, u64 x) -> u64 { return gx_body_" +
                std::to_string(i) + "(e, c, v, x); });";
     };
-    if (progs.size() > 1)
+    /* the stealing skeleton keeps its walk's state live across chunks: its chunk loops go out of line too */
+    const bool ool = progs.size() > 1 || sched;
+    if (ool)
         for (size_t i = 0; i < progs.size(); i++)
             src += "__device__ __noinline__ void gx_chunk_" + std::to_string(i) +
                    "(const gx_chunk ch, u32 wcp, u32 shard_off, u64 *ctx_all) {\n"
@@ -753,7 +755,7 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
                    chunk_loop(i) + "\n}\n";
     std::string body = std::string("  gx::") + (sched ? "exec_steal" : "exec_tiles") +
                        "(P, [](const gx::ExecEnv &env, const gx_chunk &ch, gx::u64 *ctx_all) {\n";
-    if (progs.size() == 1) {
+    if (!ool) {
         body += "    using namespace gx;\n    " + chunk_loop(0) + "\n";
     } else {
         body += "    extern __shared__ __align__(16) uint8_t smem_base[];\n    switch (env.slot) {\n";
