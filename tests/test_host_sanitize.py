@@ -149,3 +149,21 @@ def test_sanitized_oracle_catches_a_planted_bounds_bug(corpus_file, tmp_path):
     _compile(["gcc", "-std=c11"] + SAN + [str(tmp_path / "tests" / "host" / "oracle_sanitize.c"), "-o", str(exe)])
     r = subprocess.run([str(exe), str(corpus_file), "8"], capture_output=True, text=True, timeout=600, env=ENV)
     assert r.returncode != 0 and "AddressSanitizer" in r.stderr, (r.stdout[-500:], r.stderr[-2000:])
+
+
+def test_sanitized_verifier_catches_a_planted_bounds_bug(corpus_file, tmp_path):
+    """The same for the verifier: in a copy that no longer refuses jumps past the last
+    instruction, the corpus's mutants make AddressSanitizer report."""
+    if not shutil.which("g++"):
+        pytest.skip("no host compiler")
+    csrc = os.path.join(ROOT, "paper_2512_12615_gb300", "csrc")
+    src = open(os.path.join(csrc, "verifier.cpp")).read()
+    old = 'if (tgt < 0 || tgt >= (s64)n) return fail(pc, "jump out of range");'
+    assert src.count(old) == 1
+    mutant = tmp_path / "verifier.cpp"
+    mutant.write_text(src.replace(old, 'if (tgt < 0) return fail(pc, "jump out of range");'))
+    exe = tmp_path / "verify_mutant"
+    _compile(["g++", "-std=c++17"] + SAN + ["-I" + os.path.join(ROOT, "include"), "-I" + csrc, str(mutant),
+              os.path.join(csrc, "decode.cpp"), os.path.join(HERE, "host", "verify_sanitize.cpp"), "-o", str(exe)])
+    r = subprocess.run([str(exe), str(corpus_file), "8"], capture_output=True, text=True, timeout=600, env=ENV)
+    assert r.returncode != 0 and "AddressSanitizer" in r.stderr, (r.stdout[-500:], r.stderr[-2000:])
