@@ -122,7 +122,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.replace(tmp, LIB)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
+    _remove_stale_objects(set(objs))
     return LIB
+
+
+def _remove_stale_objects(keep) -> None:
+    """Objects of earlier source versions (their names carry a stamp) are not kept."""
+    for name in os.listdir(BUILD):
+        path = os.path.join(BUILD, name)
+        if name.endswith(".o") and name != "gx_embed.o" and path not in keep:
+            try:
+                os.remove(path)
+            except OSError:
+                pass
 
 
 if __name__ == "__main__":

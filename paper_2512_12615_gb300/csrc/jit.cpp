@@ -10,11 +10,15 @@
  * runtime's library API.  A kernel may hold several programs (a batch): it switches on
  * the chunk's program slot.  NVRTC is loaded with dlopen, so the engine library keeps
  * loading on hosts without the compiler or a GPU; compiled cubins are cached in memory
- * and, if GX_JIT_CACHE names a directory, on disk.  If GX_JIT_DUMP_DIR names a directory,
- * every generated source is also written there as <key>.cu, for reading.
+ * and, if GX_JIT_CACHE names a directory, on disk.  The disk cache is bounded: after each
+ * write, the oldest cubins are removed until the directory holds at most GX_JIT_CACHE_MB
+ * megabytes (default 1024).  If GX_JIT_DUMP_DIR names a directory, every generated source
+ * is also written there as <key>.cu, for reading.
  */
 #include <cuda_runtime.h>
+#include <dirent.h>
 #include <dlfcn.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 #include <sys/stat.h>
@@ -701,6 +705,38 @@ void write_file(const std::string &path, const std::vector<char> &data) {
     else remove(tmp.c_str());
 }
 
+/* keep the disk cache within GX_JIT_CACHE_MB (default 1 GiB): remove the least recently
+   written cubins first */
+void trim_cache(const std::string &dir) {
+    const char *mb = getenv("GX_JIT_CACHE_MB");
+    const uint64_t cap = (mb && *mb ? strtoull(mb, nullptr, 10) : 1024ULL) << 20;
+    DIR *d = opendir(dir.c_str());
+    if (!d) return;
+    struct Entry {
+        std::string path;
+        time_t mtime;
+        uint64_t bytes;
+    };
+    std::vector<Entry> es;
+    uint64_t total = 0;
+    while (struct dirent *e = readdir(d)) {
+        const std::string name = e->d_name;
+        if (name.size() < 7 || name.compare(name.size() - 6, 6, ".cubin") != 0) continue;
+        struct stat st;
+        const std::string path = dir + "/" + name;
+        if (stat(path.c_str(), &st) != 0) continue;
+        es.push_back({path, st.st_mtime, (uint64_t)st.st_size});
+        total += (uint64_t)st.st_size;
+    }
+    closedir(d);
+    if (total <= cap) return;
+    std::sort(es.begin(), es.end(), [](const Entry &a, const Entry &b) { return a.mtime < b.mtime; });
+    for (const Entry &e : es) {
+        if (total <= cap) break;
+        if (remove(e.path.c_str()) == 0) total -= e.bytes;
+    }
+}
+
 } // namespace
 
 std::string jit_source(const std::vector<const JitProgram *> &progs, std::string &log, int &rc,
@@ -826,6 +862,7 @@ int jit_cubin(const std::string &src, const std::string &key, std::vector<char> 
     if (!path.empty()) {
         mkdir(dir, 0755);
         write_file(path, cubin);
+        trim_cache(dir);
     }
     return GX_OK;
 }

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import tempfile
 from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -172,11 +173,21 @@ _SIGS = {
 _lib: Optional[ctypes.CDLL] = None
 
 
+def default_jit_cache() -> str:
+    """Where compiled programs are cached on disk unless GX_JIT_CACHE says otherwise:
+    $XDG_CACHE_HOME/gx-jit, else a per-user folder under the system temporary directory.
+    Never inside the package tree, so the source tree stays small whatever is compiled."""
+    base = os.environ.get("XDG_CACHE_HOME")
+    if base:
+        return os.path.join(base, "gx-jit")
+    return os.path.join(tempfile.gettempdir(), f"gx-jit-{os.getuid()}")
+
+
 def lib() -> ctypes.CDLL:
     """Load the native library (building it first if it is absent or stale)."""
     global _lib
     if _lib is None:
-        os.environ.setdefault("GX_JIT_CACHE", os.path.join(_build.BUILD, "jit"))
+        os.environ.setdefault("GX_JIT_CACHE", default_jit_cache())
         path = _build.build()
         L = ctypes.CDLL(path)
         for name, (res, args) in _SIGS.items():
