@@ -32,6 +32,10 @@
  *     {u32 len; u32 flags (bit0 = discarded); u64 event_idx}, payload padded to 8;
  *   - ringbuf_output returns -EAGAIN (-11) when the ring is full; reserve returns NULL
  *     and both count a drop;
+ *   - a ring closes at the first record that does not fit: that reservation and every
+ *     later one fail (and count a drop), whatever their size, until the ring is drained.
+ *     The records kept are a prefix of the reservations, so the data is one contiguous
+ *     run from the start of the ring;
  *   - array update with key >= max_entries -> -E2BIG, NOEXIST -> -EEXIST, delete ->
  *     -EINVAL; hash update NOEXIST on a present key -> -EEXIST, EXIST on an absent key ->
  *     -ENOENT, insert beyond max_entries -> -E2BIG; hash delete of an absent key -> -ENOENT;
@@ -78,6 +82,7 @@ typedef struct or_map {
     hnode *all;
     uint8_t *ring; /* ring buffer: max_entries bytes */
     uint64_t ring_used, dropped;
+    int ring_closed; /* a reservation did not fit: every later one fails until a drain */
 } or_map;
 
 static uint64_t fnv1a(const uint8_t *p, uint32_t n) {
@@ -292,6 +297,7 @@ void or_ringbuf_reset(or_map *m) {
     memset(m->ring, 0, m->max_entries);
     m->ring_used = 0;
     m->dropped = 0;
+    m->ring_closed = 0;
 }
 
 /* ------------------------------------------------------------------ deferred updates */
@@ -556,7 +562,12 @@ static or_map *map_arg(const hctx *h, uint64_t v) {
 
 static uint8_t *rb_reserve(or_map *m, uint64_t size, uint64_t event_idx) {
     uint64_t rec = 16 + ((size + 7) & ~7ULL);
-    if (size == 0 || size > 0xFFFFFFFFULL || m->ring_used + rec > m->max_entries) {
+    if (size == 0 || size > 0xFFFFFFFFULL) {
+        m->dropped++;
+        return NULL;
+    }
+    if (m->ring_closed || m->ring_used + rec > m->max_entries) {
+        m->ring_closed = 1;
         m->dropped++;
         return NULL;
     }

@@ -25,6 +25,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <sstream>
@@ -696,7 +697,10 @@ bool read_file(const std::string &path, std::vector<char> &out) {
 }
 
 void write_file(const std::string &path, const std::vector<char> &data) {
-    std::string tmp = path + ".tmp" + std::to_string((unsigned long)getpid());
+    /* a name of its own per writer (process and call), so concurrent writers of one key never
+       share a temporary file; the rename publishes a complete file */
+    static std::atomic<unsigned long> seq{0};
+    std::string tmp = path + ".tmp" + std::to_string((unsigned long)getpid()) + "." + std::to_string(seq++);
     FILE *f = fopen(tmp.c_str(), "wb");
     if (!f) return;
     bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
@@ -843,8 +847,11 @@ int jit_cubin(const std::string &src, const std::string &key, std::vector<char> 
         log = "jit: nvrtcCreateProgram failed";
         return GX_E_CUDA;
     }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG", "-w"};
-    int rc = nv.compile(prog, 5, opts);
+    /* split compilation: the compiler optimises the kernel entries and out-of-line functions
+       (one per program in a batch) on parallel threads */
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG", "-w",
+                          "--split-compile=0"};
+    int rc = nv.compile(prog, 6, opts);
     size_t ls = 0;
     nv.log_size(prog, &ls);
     std::string clog(ls, '\0');

@@ -369,6 +369,21 @@ def jit_check(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, deter
     return rc, log.value.decode()
 
 
+def precompile(programs: Sequence[Tuple], deterministic: bool = True, threads: Optional[int] = None) -> List[int]:
+    """Host-only: compile the specialised form of many programs at once, one host thread per
+    program (gx_jit_check each), so that loading them afterwards reads the disk cache
+    (GX_JIT_CACHE) instead of compiling one after another.  `programs` holds
+    (insns, map specs, ctx_size) triples; returns each one's status."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    lib()
+    items = list(programs)
+    if not items:
+        return []
+    with ThreadPoolExecutor(max_workers=threads or min(len(items), os.cpu_count() or 1)) as ex:
+        return [rc for rc, _ in ex.map(lambda t: jit_check(t[0], t[1], t[2], deterministic=deterministic), items)]
+
+
 class Context:
     def __init__(self, device: int = 0, mem_budget: int = 0) -> None:
         h = ctypes.c_void_p()

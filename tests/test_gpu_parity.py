@@ -150,6 +150,64 @@ def test_ringbuf_drops(ctx):
     assert len(gx.parse_records(raw)) == 10 and dropped == 0
 
 
+def _mixed_ring_program():
+    """Reserves 8, 48 or 200 payload bytes (records of 24, 64 and 216 bytes) by ctx word 1,
+    writes ctx word 0 into the payload, submits; R0 = 1 if the reservation succeeded."""
+    lines = ["mov r6 r1", "ldx8 r8 r6 0", "ldx8 r7 r6 8", "jeq r7 0 mid", "jeq r7 1 big"]
+    for label, size in ((None, 8), ("mid", 48), ("big", 200)):
+        lines += ([f"{label}:"] if label else []) + [
+            "ld_map r1 0", f"mov r2 {size}", "mov r3 0", "call ringbuf_reserve", "jeq r0 0 out", "stx8 r0 0 r8",
+            "mov r1 r0", "mov r2 0", "call ringbuf_submit", "mov r0 1", "exit"]
+    return assemble(lines + ["out:", "exit"]).prog()
+
+
+@pytest.mark.parametrize("jit", [False, True])
+def test_ringbuf_mixed_sizes_overflow(ctx, jit):
+    """Mixed record sizes into an 8 KiB ring, 3,000 events: the ring closes at the first record
+    that does not fit (the oracle's rule), so what the device keeps is a valid outcome of a
+    concurrent run.  Against the oracle with a ring large enough for everything: every kept
+    record is one of its records, byte for byte; kept + dropped = all of them; R0 says which
+    were kept; the kept records fill the ring to within one largest record.  The oracle's own
+    8 KiB run obeys the same bounds."""
+    import paper_2512_12615_gb300 as gx
+
+    cap, n = 8192, 3000
+    prog = _mixed_ring_program()
+    rng = np.random.default_rng(0x51)
+    ev = np.zeros((n, 2), dtype=np.uint64)
+    ev[:, 0] = rng.integers(1, 1 << 62, n, dtype=np.uint64)
+    ev[:, 1] = rng.integers(0, 3, n)
+    rec_of = {0: 64, 1: 216, 2: 24}
+    om = O.maps_from_specs([dict(type=27, key_size=0, value_size=0, max_entries=1 << 20)])
+    r0_all, _ = O.run(prog, om, ev, 16, want_r0=True)
+    every, d_all = om[0].ringbuf_records()
+    assert d_all == 0 and len(every) == n and all(int(x) == 1 for x in r0_all)
+    every = dict(every)
+    ob = O.maps_from_specs([dict(type=27, key_size=0, value_size=0, max_entries=cap)])
+    r0_o, _ = O.run(prog, ob, ev, 16, want_r0=True)
+    kept_o, dropped_o = ob[0].ringbuf_records()
+    used_o = sum(rec_of[int(ev[i, 1])] for i, _ in kept_o)
+    assert [i for i, _ in kept_o] == list(range(len(kept_o)))  # sequential: a prefix, then closed
+    assert len(kept_o) + dropped_o == n and cap - 216 < used_o <= cap
+    m = gpu_maps(ctx, [dict(type=27, key_size=0, value_size=0, max_entries=cap)])
+    p = gx.Program(ctx, prog, m, 16, jit=jit)
+    ret = torch.zeros(n, dtype=torch.int64, device="cuda")
+    p.run(device_events(ev), n, ret_out=ret)
+    assert p.status().status == 0
+    raw, dropped = m[0].drain()
+    recs = gx.parse_records(raw)
+    idx = [i for i, _ in recs]
+    assert len(set(idx)) == len(idx)
+    assert all(every[i] == pl for i, pl in recs)
+    assert len(recs) + dropped == n
+    r0 = ret.cpu().numpy()
+    assert set(np.nonzero(r0 == 1)[0].tolist()) == set(idx) and set(np.unique(r0).tolist()) <= {0, 1}
+    used = sum(rec_of[int(ev[i, 1])] for i in idx)
+    assert cap - 216 < used <= cap
+    p.destroy()
+    m[0].destroy()
+
+
 def test_budget_trip_is_reported_not_hung(ctx):
     import paper_2512_12615_gb300 as gx
 
