@@ -4,7 +4,10 @@
 Headline (one JSON line on stdout): the page-heat policy (~90-slot program with an
 8-trip loop, hash map of 1M entries + per-kind array tally) over 64M 32-byte events with
 Zipf(1.1) page addresses over a 64 GiB space; one step = one plain launch of the
-interpreter over the whole batch, maps resident across steps.  The line also carries
+load-time specialised program over the whole batch, maps resident across steps (the
+interpreter's figures are under "configs").  After the timed steps the maps are checked
+against the closed form of the policy at full size ("parity"); a mismatch fails the run.
+The line also carries
 the roofline of that kernel, the oracle's CPU throughput on a bounded sample, the same
 metric end to end through host buffers, the clocks seen during the timed region and,
 under "configs", the other workloads: counting (1M events, L2 flushed between reps),
@@ -39,9 +42,10 @@ C2_EVENTS = 64 << 20
 C1_EVENTS = 1 << 20
 C3_PAIRS = 128 << 20
 SEED = 0x6758
-# DRAM bytes (read + write) per event of the specialised page-heat kernel, from one ncu capture of
-# 16M events (profiles/gx_jit_kernel_pageheat_16M.md); traffic grows with the events streamed, so a
-# launch's traffic is this figure times its events.  Re-take it whenever that kernel changes.
+# DRAM bytes (read + write) per event of the specialised page-heat kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a 16M-event launch; traffic grows with the
+# events streamed, so a launch's traffic is this figure times its events.  Re-take it whenever
+# that kernel changes.
 PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (543.458048e6 + 11.761152e6) / 16777216
 PAGEHEAT_WORKLOAD = ("page-heat policy, 64M events/GPU, Zipf(1.1) 4 KiB pages over 64 GiB, "
                      "hash map 1M entries (u64 -> {count, last_ts}), 8-trip loop")
@@ -137,6 +141,56 @@ class EventTimer:
         return self.a.elapsed_time(self.b)
 
 
+# ---------------------------------------------------------------------------- full-size result checks
+def check_pageheat(maps, ev, launches: int) -> dict:
+    """The maps after `launches` launches over the whole batch against the closed form of
+    page-heat (tests/closed_forms.py: group-by of addr >> 21 of (sum of weights, max ts), and
+    the per-kind tally), counts scaled by the launch count.  Bit-exact."""
+    from tests import closed_forms as CF
+
+    heat, tally = CF.page_heat(ev)
+    got = maps[0].hash_items()
+    bad_keys = set(got) ^ {int(k).to_bytes(8, "little") for k in heat}
+    bad_vals = 0
+    for k, (c, t) in heat.items():
+        v = got.get(int(k).to_bytes(8, "little"))
+        if v is not None and (int.from_bytes(v[:8], "little") != c * launches or
+                              int.from_bytes(v[8:16], "little") != t):
+            bad_vals += 1
+    tally_ok = bool(np.array_equal(maps[1].array_u64(), tally * np.uint64(launches)))
+    ok = not bad_keys and bad_vals == 0 and tally_ok
+    return {"ok": ok, "what": "hash map and tally vs closed form x launches", "launches": launches,
+            "keys": len(heat), "keys_differing": len(bad_keys), "values_differing": bad_vals, "tally_ok": tally_ok}
+
+
+def parse_ring_fixed(raw: bytes, payload: int):
+    """Records of one payload size from a drained ring: (event indices, payload bytes rows)."""
+    rec = 16 + ((payload + 7) & ~7)
+    a = np.frombuffer(raw, dtype=np.uint8)
+    assert a.size % rec == 0, "ring stream is not a whole number of records"
+    a = a.reshape(-1, rec)
+    lens = a[:, :4].copy().view("<u4")[:, 0]
+    assert (lens == payload).all(), "unexpected record length"
+    return a[:, 8:16].copy().view("<u8")[:, 0], a[:, 16:16 + payload]
+
+
+def check_latency(maps, ev, launches: int, raw_last: bytes, dropped_last: int) -> dict:
+    """The histogram after `launches` launches against the closed form (2-D histogram of
+    kernel id and floor(log2(latency))) times the launch count, and the last launch's drained
+    outlier records, sorted by pair index, against the closed form's outliers byte for byte."""
+    from tests import closed_forms as CF
+
+    hist, sel, recs = CF.latency_arrays(ev)
+    hist_ok = bool(np.array_equal(maps[0].array_u64()[:, 0], hist * np.uint64(launches)))
+    idx, pay = parse_ring_fixed(raw_last, CF.OUTLIER_DTYPE.itemsize)
+    order = np.argsort(idx, kind="stable")
+    ring_ok = (dropped_last == 0 and len(idx) == len(sel) and bool(np.array_equal(idx[order], sel)) and
+               bool(np.array_equal(pay[order], recs.view(np.uint8).reshape(len(recs), -1))))
+    return {"ok": hist_ok and ring_ok, "what": "histogram vs closed form x launches; last launch's outlier "
+                                               "records vs closed form, sorted by pair index",
+            "launches": launches, "hist_ok": hist_ok, "ring_ok": ring_ok, "outliers": int(len(sel))}
+
+
 def oracle_insns(prog, specs, cs, ev, n_sample) -> float:
     import oracle as O
 
@@ -174,9 +228,12 @@ def run_headline(args, gx, torch, dist_env, jit=True):
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
     block, ept, shards = prog.autotune(dev, C2_EVENTS, stream=sid)
     variant = getattr(prog, "tuned_variant", 0)
+    grid = "one wave" if getattr(prog, "tuned_grid", 0) == 0 else "one block per chunk"
     torch.cuda.synchronize()
+    launches = 0  # every launch into the resident maps, for the full-size result check
     for _ in range(args.warmup):
         prog.run(dev, C2_EVENTS, stream=sid)
+        launches += 1
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -194,16 +251,19 @@ def run_headline(args, gx, torch, dist_env, jit=True):
                 prog.run(dev, C2_EVENTS, stream=sid)
             per.append(t)
     total_ms = t_all.ms()
+    launches += reps
     launch_ms = [t.ms() for t in per]
     # keep sampling clocks over a longer busy window so the summary has samples
     t_end = time.time() + 1.5
     while time.time() < t_end:
         for _ in range(20):
             prog.run(dev, C2_EVENTS, stream=sid)
+            launches += 1
         torch.cuda.synchronize()
     clk = clocks.stop()
     st = prog.status()
     assert st.status == 0, f"device status {st.status}"
+    parity = check_pageheat(maps, ev, launches)
     total_ms, _ = job_rate(torch, total_ms, world, C2_EVENTS * reps, device="cuda")
     ms_step = total_ms / reps
     value = world * C2_EVENTS / (ms_step / 1e3) / 1e6
@@ -242,10 +302,11 @@ def run_headline(args, gx, torch, dist_env, jit=True):
                      "peak_kind": peak_kind,
                      "kernel": "gx_jit_kernel" if jit else "gx_exec_kernel", "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": round(avg_launch, 4)},
-        "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept, "shards": shards, "variant": variant},
+        "clocks": clk, "e2e": e2e, "launch_shape": {"block": block, "ept": ept, "shards": shards, "variant": variant, "grid": grid},
         "insns_per_event": round(insns_per_event, 2),
         "Minsns_per_s": round(value * insns_per_event, 1),
         "Mevents_per_s_geomean_steps": round(geomean_steps, 1),
+        "parity": parity,
     }
     prog.destroy()
     for m in maps:
@@ -292,7 +353,6 @@ def run_latency(gx, torch, jit=True, pairs=None):
     prog_i, specs, cs = P.latency()
     ev = gen.latency_pairs(pairs, seed=SEED)
     dev = to_device(ev)
-    del ev
     ctx = gx.Context(torch.cuda.current_device())
     maps = [gx.Map.from_spec(ctx, s) for s in specs]
     prog = gx.Program(ctx, prog_i, maps, cs, deterministic=True, jit=jit)
@@ -310,6 +370,9 @@ def run_latency(gx, torch, jit=True, pairs=None):
         if r >= 2:
             times.append(ms)
     clk = clocks.stop()
+    assert prog.status().status == 0
+    parity = check_latency(maps, ev, 8, raw, dropped)
+    del ev
     ms = float(np.median(times))
     nbytes = pairs * 64 + len(raw)
     peak, _ = peaks()
@@ -319,7 +382,7 @@ def run_latency(gx, torch, jit=True, pairs=None):
            "kernel_ms_median": round(ms, 4), "GBps": round(nbytes / ms / 1e6, 1),
            "hbm_frac": round(nbytes / ms / 1e6 / peak, 4), "ringbuf_bytes": len(raw), "dropped": dropped,
            "launch": dict(zip(("block", "ept", "shards", "variant"), tuned)), "clocks": clk,
-           "kernel_ms_all": [round(t, 4) for t in times]}
+           "kernel_ms_all": [round(t, 4) for t in times], "parity": parity}
     prog.destroy()
     for m in maps:
         m.destroy()
@@ -658,7 +721,7 @@ def main() -> int:
         try:
             it = run_headline(args, gx, torch, (rank, world), jit=False)
             configs["page_heat_interpreter"] = {k: it[k] for k in ("value", "ms_per_step", "roofline", "launch_shape",
-                                                                   "Minsns_per_s")}
+                                                                   "Minsns_per_s", "parity")}
         except Exception as e:
             configs["page_heat_interpreter"] = {"error": repr(e)}
     cpu = None
@@ -688,8 +751,13 @@ def main() -> int:
                 "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"], "clocks": head["clocks"],
                 "gpu_launches": head["gpu_launches"], "insns_per_event": head["insns_per_event"],
                 "Minsns_per_s": head["Minsns_per_s"],
-                "Mevents_per_s_geomean_steps": head["Mevents_per_s_geomean_steps"], "configs": configs}
+                "Mevents_per_s_geomean_steps": head["Mevents_per_s_geomean_steps"], "parity": head["parity"],
+                "configs": configs}
         print(json.dumps(line), flush=True)
+        # a full-size result that differs from its closed form fails the run
+        checked = [head["parity"]] + [c["parity"] for c in configs.values() if isinstance(c, dict) and "parity" in c]
+        if not all(c["ok"] for c in checked):
+            return 1
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -200,7 +200,13 @@ int gx_map_read(gx_map *map, void *host_out, uint64_t cap_bytes, uint64_t *n_out
  * gx_map_read for hash maps; synchronises `stream`.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the rest of the process: after a
+ *     cudaDeviceReset of that device it is stale, so do not call this entry point again
+ *     in a process that reset the device.
+ *   - With lazy module loading (CUDA's default), the array itself is allocated when the
+ *     library's device code is first loaded on a device, which may be this entry point's
+ *     first call.  A caller that will have no memory to spare later should make one call
+ *     early (any engine call that launches work on the device also loads it).
  *   - Every call shares the array and clears its counter: calls whose GPU work overlaps
  *     (other streams or host threads) race on it.
  *   - GX_EINVAL for array or ring-buffer maps.  GX_E2BIG, with *n_out = the live pair
@@ -416,7 +422,10 @@ uint32_t gx_prog_uops(const gx_prog *prog);
 typedef struct gx_launch {
     uint32_t block;  /* threads per block: 64..1024, multiple of 32; 0 = tuned/default */
     uint32_t ept;    /* events per thread: 1..64; 0 = tuned/default */
-    uint32_t grid;   /* blocks; 0 = enough for n */
+    uint32_t grid;   /* blocks: 0 = one wave (as many as the device holds at once; each block runs the
+                        chunks of block * ept events b, b + grid, ...), GX_GRID_PER_CHUNK = one block per
+                        chunk, else that many blocks (at most one per chunk); the tuner picks between
+                        one wave and one block per chunk */
     uint32_t shards; /* map-sharding width of load-time specialised programs (GX_PROG_JIT): updates of
                         combinable maps (gx_analyze) are first combined in shared memory per block,
                         small array maps whole, other maps in a cache of 2^shards entries (2..10, capped
@@ -425,13 +434,19 @@ typedef struct gx_launch {
                         for the default width) to warp-aggregate the updates that miss the cache, which
                         pays when hot values miss and costs a warp match on every miss.  Ignored by the
                         interpreter. */
-    uint32_t variant; /* specialised single programs: GX_VARIANT_WIDE (registers as the compiler likes) or
-                         GX_VARIANT_CAPPED (at most 48 registers, so five 256-thread blocks share an SM);
-                         0 = tuned/default (wide).  Ignored by the interpreter and by batches. */
+    uint32_t variant; /* specialised programs: which compiled entry runs.  Each entry is compiled for a
+                         number of resident 256-thread blocks per SM, which caps its registers per
+                         thread: GX_VARIANT_WIDE 2 blocks (<= 128 registers), GX_VARIANT_CAPPED 5 (<= 48),
+                         GX_VARIANT_3 3 (<= 80), GX_VARIANT_4 4 (<= 64).  Single programs have all four;
+                         batches have WIDE and CAPPED (their default).  0 = tuned/default (GX_VARIANT_4
+                         for a single program).  Ignored by the interpreter. */
     uint32_t reserved;
 } gx_launch;
 #define GX_VARIANT_WIDE 1u
 #define GX_VARIANT_CAPPED 2u
+#define GX_VARIANT_3 3u
+#define GX_VARIANT_4 4u
+#define GX_GRID_PER_CHUNK 0xFFFFFFFFu
 #define GX_SHARDS_OFF 255u
 #define GX_SHARDS_AGG 0x100u
 

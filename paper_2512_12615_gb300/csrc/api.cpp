@@ -122,7 +122,7 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
                  uint64_t idx_base, int64_t *ret_out, const gx_launch &lp, cudaStream_t s) {
     uint32_t block = lp.block ? lp.block : 256, ept = lp.ept ? lp.ept : 4;
     if (block < 32 || block > GX_MAX_BLOCK || block % 32 || ept < 1 || ept > 64) return GX_EINVAL;
-    if (lp.variant > GX_VARIANT_CAPPED) return GX_EINVAL;
+    if (lp.variant > GX_VARIANT_4) return GX_EINVAL;
     uint32_t area = (uint32_t)round_up(image_bytes, 16);
     uint64_t smem = exec_smem(area, block, p->opts.ctx_size);
     uint32_t wc = 0, shard_off = 0;
@@ -135,9 +135,40 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     }
     int rc = ensure_smem(p->ctx, smem);
     if (rc) return rc;
-    uint64_t per_block = (uint64_t)block * ept;
-    uint64_t grid = (n + per_block - 1) / per_block;
-    if (lp.grid && lp.grid < grid) return GX_EINVAL; /* a fixed grid must still cover n */
+    const uint64_t per_block = (uint64_t)block * ept;
+    const uint64_t chunks = (n + per_block - 1) / per_block;
+    uint64_t grid = chunks;
+    if (lp.grid != GX_GRID_PER_CHUNK) {
+        uint64_t cap = lp.grid;
+        if (cap == 0) { /* one wave: the blocks the device holds at once loop over the chunks */
+            const uint64_t key = ((uint64_t)block << 40) | (smem << 3) | lp.variant;
+            int occ = 0;
+            bool known = false;
+            {
+                std::lock_guard<std::mutex> g(p->ctx->mu);
+                auto it = p->occupancy.find(key);
+                if (it != p->occupancy.end()) {
+                    occ = it->second;
+                    known = true;
+                }
+            }
+            if (!known) {
+                if (p->jit) rc = cuda_status(jit_set_smem(p->jk, smem));
+                cudaError_t e = rc ? cudaSuccess
+                                   : p->jit ? jit_occupancy(p->jk, (int)block, smem, &occ, lp.variant)
+                                            : exec_occupancy((int)block, smem, &occ);
+                if (rc == GX_OK && e != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = GX_E_CUDA;
+                }
+                if (rc) return rc;
+                std::lock_guard<std::mutex> g(p->ctx->mu);
+                p->occupancy[key] = occ;
+            }
+            cap = (uint64_t)p->ctx->sms * (uint64_t)(occ > 0 ? occ : 1);
+        }
+        grid = std::min<uint64_t>(chunks, cap);
+    }
     if (grid > 0x7FFFFFFFull) return GX_E2BIG;
     ExecParams P;
     memset(&P, 0, sizeof P);
@@ -156,7 +187,7 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     if (p->jit) {
         rc = cuda_status(jit_set_smem(p->jk, smem));
         if (rc == GX_OK)
-            rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s, lp.variant == GX_VARIANT_CAPPED));
+            rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s, lp.variant));
     } else {
         rc = cuda_status(launch_exec(P, (unsigned)grid, block, smem, s));
     }
@@ -923,11 +954,21 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
         /* policy only: the sharding choice at one shape on a smaller sample (batch planning) */
         const uint64_t sample = std::min<uint64_t>(n, policy_only ? (1ull << 21) : (1ull << 26));
         const std::vector<uint32_t> blocks = policy_only ? std::vector<uint32_t>{256} : std::vector<uint32_t>{128, 256};
-        const std::vector<uint32_t> epts =
-            policy_only ? std::vector<uint32_t>{8} : std::vector<uint32_t>{2, 4, 8, 16, 32};
-        /* specialised single programs: the wide and the register-capped entry */
+        /* (events per thread, grid): one wave of blocks looping over chunks of every size, and
+           one block per chunk at two sizes */
+        const std::vector<std::pair<uint32_t, uint32_t>> epts =
+            policy_only ? std::vector<std::pair<uint32_t, uint32_t>>{{8, 0}}
+                        : std::vector<std::pair<uint32_t, uint32_t>>{{1, 0}, {2, 0}, {4, 0}, {8, 0}, {16, 0}, {32, 0},
+                                                                     {64, 0}, {8, GX_GRID_PER_CHUNK},
+                                                                     {32, GX_GRID_PER_CHUNK}};
+        /* specialised single programs: every compiled entry, wide to register-capped */
         std::vector<uint32_t> variants = {0};
-        if (!policy_only && p->jit && p->jk.kernel_capped) variants = {GX_VARIANT_WIDE, GX_VARIANT_CAPPED};
+        if (!policy_only && p->jit) {
+            variants.clear();
+            for (uint32_t v = 1; v < 5; v++)
+                if (p->jk.variant[v]) variants.push_back(v);
+            if (variants.empty()) variants = {0};
+        }
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -960,8 +1001,8 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
         };
         std::vector<std::pair<float, gx_launch>> ranked;
         for (uint32_t b : blocks)
-            for (uint32_t e : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
-                const gx_launch l = {b, e, 0, w, v, 0};
+            for (const auto &eg : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
+                const gx_launch l = {b, eg.first, eg.second, w, v, 0};
                 const float ms = timed(l, sample, 3);
                 if (ms >= 0) ranked.push_back({ms, l});
             }

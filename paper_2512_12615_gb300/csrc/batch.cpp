@@ -142,6 +142,7 @@ struct Persist {
      * sizes the combining area.
      */
     uint32_t alloc_bits = 0;
+    uint32_t variant = 0; /* the multi-program kernel's entry (GX_VARIANT_*; 0 = its default, capped) */
     int build(gx_ctx *c, uint32_t blk, uint32_t image_area, uint32_t ctx_max, uint64_t chunks, uint32_t shards = 0,
               uint32_t alloc_wc = 0) {
         release();
@@ -160,7 +161,7 @@ struct Persist {
         int rc = jk ? cuda_status(jit_set_smem(*jk, smem)) : ensure_smem(c, smem);
         if (rc) return rc;
         int occ = 0;
-        cudaError_t oe = jk ? jit_occupancy(*jk, (int)block, smem, &occ) : exec_occupancy((int)block, smem, &occ);
+        cudaError_t oe = jk ? jit_occupancy(*jk, (int)block, smem, &occ, variant) : exec_occupancy((int)block, smem, &occ);
         if (oe != cudaSuccess || occ < 1) {
             cudaGetLastError();
             return GX_E_CUDA;
@@ -203,7 +204,7 @@ struct Persist {
         if (rc == GX_OK) {
             cudaMemsetAsync(cursor(), 0, 4, cs);
             if (sched) cudaMemsetAsync(steal_next(), 0, steal_bytes(), cs);
-            if (jk) jit_launch(*jk, P, grid, block, smem, cs);
+            if (jk) jit_launch(*jk, P, grid, block, smem, cs, variant);
             else launch_exec(P, grid, block, smem, cs);
             if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) rc = GX_E_CUDA;
         }
@@ -318,7 +319,7 @@ int gx_batch_add(gx_batch *b, gx_prog *p, const void *events, uint64_t n, int64_
     return GX_OK;
 }
 
-static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t shards) {
+static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t shards, uint32_t variant = 0) {
     uint32_t area = 0, max_ctx = 8;
     for (auto &it : b->items) {
         area = std::max(area, it.prog->image_bytes);
@@ -334,6 +335,7 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t 
     /* one kernel holds every program: a wide cache would cost all of them occupancy */
     alloc = std::min(alloc, dflt);
     b->persist.jk = b->jit ? &b->jk : nullptr;
+    b->persist.variant = b->jit ? variant : 0;
     b->persist.sched = b->sched;
     b->persist.sched_budget = b->sched_budget;
     b->persist.launch_control = (b->sched_flags & GX_SCHED_F_LAUNCH_CONTROL) != 0;
@@ -346,7 +348,7 @@ static int batch_plan_shape(gx_batch *b, uint32_t block, uint32_t ept, uint32_t 
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->persist.nchunks(), &nch, 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return GX_E_CUDA;
-    b->shape = gx_launch{block, ept, b->persist.grid, shards};
+    b->shape = gx_launch{block, ept, b->persist.grid, shards, b->persist.variant, 0};
     return GX_OK;
 }
 
@@ -360,7 +362,8 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
         uint32_t blk = lp->block ? lp->block : 256, ept = lp->ept ? lp->ept : 4;
         if (blk < 64 || blk > GX_MAX_BLOCK || blk % 32 || ept < 1 || ept > 64) return GX_EINVAL;
         if (!shards_valid(lp->shards)) return GX_EINVAL;
-        int rc = batch_plan_shape(b, blk, ept, lp->shards);
+        if (lp->variant != 0 && lp->variant != GX_VARIANT_WIDE && lp->variant != GX_VARIANT_CAPPED) return GX_EINVAL;
+        int rc = batch_plan_shape(b, blk, ept, lp->shards, lp->variant);
         if (rc == GX_OK) b->planned = true;
         return rc;
     }
@@ -401,9 +404,12 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
         const uint32_t blocks[] = {128, 256};
         const uint32_t epts[] = {2, 4, 8, 16};
         std::vector<uint32_t> widths = {0}; /* per-program choices ride on the chunks */
+        /* the multi-program kernel's wide and capped entries */
+        std::vector<uint32_t> variants = {0};
+        if (b->jit && b->jk.variant[GX_VARIANT_WIDE]) variants = {GX_VARIANT_CAPPED, GX_VARIANT_WIDE};
         for (uint32_t blk : blocks)
-            for (uint32_t ept : epts) for (uint32_t w : widths) {
-                if (batch_plan_shape(b, blk, ept, w) != GX_OK) continue;
+            for (uint32_t ept : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
+                if (batch_plan_shape(b, blk, ept, w, v) != GX_OK) continue;
                 b->persist.launch(s); /* warm-up */
                 cudaEventRecord(e0, s);
                 b->persist.launch(s);
@@ -413,7 +419,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = gx_launch{blk, ept, 0, w};
+                    best = gx_launch{blk, ept, 0, w, v, 0};
                 }
             }
         cudaEventDestroy(e0);
@@ -426,7 +432,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
     }
     for (size_t i = 0; i < maps.size(); i++) dfree(b->ctx, saved[i], maps[i]->dbytes);
     if (rc) return rc;
-    rc = batch_plan_shape(b, best.block, best.ept, best.shards);
+    rc = batch_plan_shape(b, best.block, best.ept, best.shards, best.variant);
     if (rc == GX_OK) b->planned = true;
     return rc;
 }

@@ -552,6 +552,39 @@ __device__ __forceinline__ void load_ctx_tile(u64 *ctxw, const uint8_t *events, 
     __syncwarp();
 }
 
+/*
+ * A warp's tile in flight, for records of CW = 4 or 8 words: its 32 * CW * 8 bytes as
+ * 16-byte chunks, CW / 2 per lane, held in registers.  tile_fetch issues every load of a
+ * tile at once (the loads of the next tile go out before the current tile runs, so
+ * streaming overlaps execution); tile_store transposes the chunks into the shared tile.
+ */
+template <u32 CW>
+struct Tile {
+    ulonglong2 v[CW / 2];
+};
+
+template <u32 CW>
+__device__ __forceinline__ void tile_fetch(Tile<CW> &t, const uint8_t *events, u64 first, u64 n) {
+    const u32 lane = lane_id();
+    const u64 nrec = n > first ? (n - first < 32 ? n - first : 32) : 0;
+    const ulonglong2 *src = (const ulonglong2 *)(events + first * (u64)CW * 8);
+#pragma unroll
+    for (u32 k = 0; k < CW / 2; k++) {
+        const u32 c = lane + 32u * k; /* chunk c holds words 2c, 2c + 1 of the tile */
+        t.v[k] = (2u * c) / CW < nrec ? __ldcs(src + c) : make_ulonglong2(0ull, 0ull);
+    }
+}
+
+template <u32 CW>
+__device__ __forceinline__ void tile_store(u64 *ctxw, const Tile<CW> &t) {
+    const u32 row = GX_CTX_ROW(CW), lane = lane_id();
+#pragma unroll
+    for (u32 k = 0; k < CW / 2; k++) {
+        const u32 word = 2u * (lane + 32u * k), rec = word / CW, f = word % CW;
+        ctxw[f * row + rec] = t.v[k].x;
+        ctxw[(f + 1) * row + rec] = t.v[k].y;
+    }
+}
 
 /* ------------------------------------------------------------------ kernel skeleton */
 /* what a per-event body sees: the staged program image and its maps */
@@ -673,6 +706,37 @@ __device__ __forceinline__ void chunk_tiles(const ExecEnv &env, const gx_chunk &
     }
 }
 
+/* chunk_tiles for records of CW (4 or 8) words, with the next tile's loads in flight while
+   the current tile runs */
+template <u32 CW, typename RunEvent>
+__device__ __forceinline__ void chunk_tiles_cw(const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all, RunEvent run_event) {
+    const u32 warp = threadIdx.x >> 5, lane = lane_id();
+    u64 *ctxw = ctx_all + warp * CW * GX_CTX_ROW(CW);
+    u64 first = ch.begin + (u64)warp * 32;
+    if (first >= ch.end) return;
+    Tile<CW> t;
+    tile_fetch<CW>(t, ch.events, first, ch.end);
+    for (; first < ch.end; first += blockDim.x) {
+        tile_store<CW>(ctxw, t);
+        __syncwarp();
+        const u64 next = first + blockDim.x;
+        if (next < ch.end) tile_fetch<CW>(t, ch.events, next, ch.end);
+        const u64 idx = first + lane;
+        const bool valid = idx < ch.end;
+        u64 r0 = run_event(env, ctxw, valid, ch.idx_base + idx);
+        if (valid && ch.ret_out) ch.ret_out[idx] = (long long)r0;
+        __syncwarp();
+    }
+}
+
+/* chunk_tiles for any record size, choosing the pipelined form for 32- and 64-byte records */
+template <typename RunEvent>
+__device__ __forceinline__ void chunk_tiles_any(const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all, RunEvent run_event) {
+    if (ch.ctx_size == 32) chunk_tiles_cw<4>(env, ch, ctx_all, run_event);
+    else if (ch.ctx_size == 64) chunk_tiles_cw<8>(env, ch, ctx_all, run_event);
+    else chunk_tiles(env, ch, ctx_all, run_event);
+}
+
 /* ExecEnv of the program image staged at smem */
 __device__ __forceinline__ ExecEnv stage_env_at(uint8_t *smem, u32 shard_off, u32 slot, u32 wcp) {
     const gx_dprog_hdr *hdr = (const gx_dprog_hdr *)smem;
@@ -711,23 +775,28 @@ __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunChunk run_chu
     __shared__ const uint8_t *s_image;
     u64 *ctx_all = (u64 *)(smem + P.image_area);
     if (P.mode == 0) {
+        /* chunks of blockDim * ept events; block b runs chunks b, b + gridDim, ... with the
+           image staged and the combining area open once for all of them */
         stage_image(smem, P.image, P.image_bytes);
         const ExecEnv env = stage_env(smem, P, 0, P.wc_bits);
         if (env.wc_bits) {
             wc_init(env);
             __syncthreads();
         }
+        const u64 per = (u64)blockDim.x * P.ept;
         gx_chunk ch;
         ch.image = P.image;
         ch.events = P.events;
         ch.ret_out = P.ret_out;
-        ch.begin = (u64)blockIdx.x * blockDim.x * P.ept;
-        ch.end = ch.begin + (u64)blockDim.x * P.ept < P.n ? ch.begin + (u64)blockDim.x * P.ept : P.n;
         ch.idx_base = P.idx_base;
         ch.image_bytes = P.image_bytes;
         ch.ctx_size = P.ctx_size;
         ch.pad = 0;
-        run_chunk(env, ch, ctx_all);
+        for (u64 b = (u64)blockIdx.x * per; b < P.n; b += (u64)gridDim.x * per) {
+            ch.begin = b;
+            ch.end = b + per < P.n ? b + per : P.n;
+            run_chunk(env, ch, ctx_all);
+        }
         if (env.wc_bits) {
             __syncthreads();
             wc_flush(env);
@@ -778,7 +847,7 @@ template <typename RunEvent>
 __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunEvent run_event) {
     exec_tiles(
         P,
-        [&](const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all) { chunk_tiles(env, ch, ctx_all, run_event); },
+        [&](const ExecEnv &env, const gx_chunk &ch, u64 *ctx_all) { chunk_tiles_any(env, ch, ctx_all, run_event); },
         [](const ExecEnv &) {}, [](const ExecEnv &) {});
 }
 

@@ -24,8 +24,8 @@ struct JitProgram {
 };
 
 struct JitKernel {
-    cudaKernel_t kernel = nullptr;
-    cudaKernel_t kernel_capped = nullptr; /* one program: the entry capped at 48 registers */
+    cudaKernel_t kernel = nullptr;      /* the default entry (GX_VARIANT_4 for one program, capped for several) */
+    cudaKernel_t variant[5] = {};       /* entries by GX_VARIANT_* (index 0 unused); null where not compiled */
     std::string key;
     size_t smem_attr = 0;
     uint32_t shard_bytes = 0; /* shared memory of the block-private combining area at its widest (0: none) */
@@ -80,10 +80,14 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
  */
 int check_sched_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
                         const gx_prog_opts &opts, const gx_simt_spec *limits, VerifyOut &v);
+/* the entry of a GX_VARIANT_* (0 or one not compiled: the default entry) */
+inline cudaKernel_t jit_entry(const JitKernel &k, uint32_t variant) {
+    return variant < 5 && k.variant[variant] ? k.variant[variant] : k.kernel;
+}
 cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
-                       cudaStream_t s, bool capped = false);
+                       cudaStream_t s, uint32_t variant = 0);
 cudaError_t jit_set_smem(JitKernel &k, size_t bytes);
-cudaError_t jit_occupancy(const JitKernel &k, int block, size_t smem, int *blocks_per_sm);
+cudaError_t jit_occupancy(const JitKernel &k, int block, size_t smem, int *blocks_per_sm, uint32_t variant = 0);
 
 } // namespace gx
 

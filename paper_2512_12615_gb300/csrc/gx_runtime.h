@@ -54,6 +54,7 @@ struct gx_prog {
     unsigned long long *dstats = nullptr;
     uint64_t launches = 0;
     std::map<int, gx_launch> tuned; /* log2(n) bucket -> shape */
+    std::map<uint64_t, int> occupancy; /* (block, shared bytes, variant) -> resident blocks per SM */
     uint32_t pref_shards = 0;       /* tuned gx_launch.shards of this program in batches and ticks */
     bool pref_tuned = false;
     /* load-time specialisation (GX_PROG_JIT) */

@@ -362,6 +362,9 @@ std::string stk_materialise(int lo) {
 int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &out, std::string &log) {
     const uint32_t n = (uint32_t)p.insns.size();
     std::vector<uint8_t> target(n + 1, 0);
+    std::vector<uint8_t> leader(n + 1, 0); /* first instruction of a basic block */
+    bool acyclic = true;
+    leader[0] = 1;
     for (uint32_t pc = 0; pc < n; pc++) {
         if (!p.info[pc].visited) continue;
         uint64_t w = p.insns[pc];
@@ -372,11 +375,25 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             pc++;
             continue;
         }
-        if ((cls == 5 || cls == 6) && ((op & 0xF0) != 0x80) && ((op & 0xF0) != 0x90)) {
+        if ((cls == 5 || cls == 6) && ((op & 0xF0) != 0x80)) {
+            leader[pc + 1] = 1; /* after a jump or an exit */
+            if ((op & 0xF0) == 0x90) continue;
             int64_t t = (int64_t)pc + 1 + ((cls == 6 && (op & 0xF0) == 0) ? imm : off);
             target[t] = 1;
+            leader[t] = 1;
+            if (t <= (int64_t)pc) acyclic = false;
         }
     }
+    /*
+     * Reconvergence by construction.  A program without loops (every jump forward) is
+     * emitted as a sequence of its basic blocks, block b as "if (nb_ == b) { ...; nb_ =
+     * successor; }" with nb_ the lane's next block, and an exit sets nb_ past every block
+     * instead of returning.  So every valid lane passes every block boundary, in the same
+     * order, and a __syncwarp over the valid lanes there joins lanes that took different
+     * branches before the next block.  Gotos are kept for programs with loops and for
+     * warp-level handlers (whose lanes never diverge).
+     */
+    const bool structured = acyclic && !p.warp;
     /* scalar stack unless some load / store / atomic reaches the stack at a varying offset */
     bool scalar = true;
     for (uint32_t pc = 0; pc < n; pc++)
@@ -390,6 +407,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
      * valid lane and their results are broadcast; warp helpers reduce over the valid lanes.
      */
     if (p.warp) o << "  const u32 wmask = __ballot_sync(0xFFFFFFFFu, valid);\n";
+    if (structured) o << "  const u32 vm_ = __ballot_sync(0xFFFFFFFFu, valid);\n";
     o << "  if (!valid) return 0;\n"
       << "  const u32 lane = threadIdx.x & 31;\n";
     if (p.warp) o << "  const u32 leader = (u32)__ffs(wmask) - 1u;\n  const bool lead = lane == leader;\n";
@@ -404,6 +422,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
     o << "  u64 r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0;\n"
       << "  u64 back = 0;\n"
       << "  (void)lane; (void)ev_idx; (void)back; (void)r10;\n";
+    if (structured) o << "  u32 nb_ = 0;\n";
     /* before a helper that reads stack memory through R2 / R3 */
     auto mat = [&](const InsnInfo &ii, bool r3_mem) -> std::string {
         if (!scalar) return "";
@@ -417,10 +436,12 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
     };
     const uint64_t budget = p.budget;
     auto jump = [&](uint32_t pc, int64_t tgt) -> std::string {
+        if (structured) return "nb_ = " + std::to_string(tgt) + "u;";
         std::string g = "goto L" + std::to_string(tgt) + ";";
         if (tgt <= (int64_t)pc) return "{ if (++back > " + std::to_string(budget) + "ull) goto budget_trip; " + g + " }";
         return g;
     };
+    bool block_ends = false; /* structured: the open block's last statement left it (jump or exit) */
     for (uint32_t pc = 0; pc < n; pc++) {
         const InsnInfo &ii = p.info[pc];
         uint64_t w = p.insns[pc];
@@ -428,7 +449,13 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         int dst = (int)((w >> 8) & 0xF), src = (int)((w >> 12) & 0xF);
         int off = (int)(int16_t)(uint16_t)((w >> 16) & 0xFFFF);
         int32_t imm = (int32_t)(uint32_t)(w >> 32);
-        if (target[pc]) o << "L" << pc << ":;\n";
+        if (structured && leader[pc] && ii.visited) {
+            if (pc) o << (block_ends ? "  }\n" : "  nb_ = " + std::to_string(pc) + "u; }\n") << "  __syncwarp(vm_);\n";
+            o << "  if (nb_ == " << pc << "u) {\n";
+            block_ends = false;
+        } else if (!structured && target[pc]) {
+            o << "L" << pc << ":;\n";
+        }
         if (!ii.visited) {
             if (op == 0x18) pc++;
             continue;
@@ -479,10 +506,12 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             if (code == 0x00) {
                 int64_t t = (int64_t)pc + 1 + (cls == 6 ? imm : off);
                 o << jump(pc, t);
+                block_ends = true;
                 break;
             }
             if (code == 0x90) {
-                o << "return r0;";
+                o << (structured ? "nb_ = 0xFFFFFFFFu;" : "return r0;");
+                block_ends = true;
                 break;
             }
             if (code == 0x80 && p.warp && imm >= GX_HELPER_WARP_SUM_U64 && imm <= GX_HELPER_WARP_COUNT) {
@@ -568,6 +597,12 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             bool w32 = cls == 6, x = op & 8;
             std::string s = x ? R(src) : (w32 ? hex64((uint32_t)imm) : hex64((uint64_t)(int64_t)imm));
             int64_t t = (int64_t)pc + 1 + off;
+            if (structured) {
+                o << "nb_ = " << (w32 ? "c32<" : "c64<") << c << ">(" << R(dst) << ", " << s << ") ? " << t << "u : "
+                  << pc + 1 << "u;";
+                block_ends = true;
+                break;
+            }
             o << "if (" << (w32 ? "c32<" : "c64<") << c << ">(" << R(dst) << ", " << s << ")) " << jump(pc, t);
             break;
         }
@@ -656,6 +691,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         }
         o << "\n";
     }
+    if (structured) o << "  }\n  return r0;\n"; /* the verifier rules out falling off the end */
     o << "budget_trip:\n"
       << (p.warp ? "  if (lead) atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);\n" /* one handler per warp */
                  : "  atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);\n")
@@ -679,8 +715,29 @@ std::string fnv_hex(const std::string &s) {
 struct Cached {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
-    cudaKernel_t kernel_capped = nullptr;
+    cudaKernel_t variant[5] = {};
 };
+
+/*
+ * The compiled entries: a kernel is compiled once per minimum of resident 256-thread blocks
+ * per SM (launch bounds), which caps its registers per thread.  Without a minimum the
+ * compiler may still pick few registers and spill heavily, so every entry states one.
+ * Index: GX_VARIANT_*; one program gets all four, several programs wide and capped.
+ */
+struct EntrySpec {
+    uint32_t variant;
+    const char *name;
+    int min_blocks;
+};
+const EntrySpec ENTRIES[] = {{GX_VARIANT_WIDE, "gx_jit_kernel", 2},
+                             {GX_VARIANT_CAPPED, "gx_jit_kernel_capped", 5},
+                             {GX_VARIANT_3, "gx_jit_kernel_v3", 3},
+                             {GX_VARIANT_4, "gx_jit_kernel_v4", 4}};
+
+/* plain single programs get every entry; persistent kernels the wide and the capped one */
+bool entry_built(uint32_t variant, size_t n_progs, bool sched) {
+    return (n_progs == 1 && !sched) || variant == GX_VARIANT_WIDE || variant == GX_VARIANT_CAPPED;
+}
 std::mutex cache_mu;
 std::map<std::string, Cached> cache;
 
@@ -780,8 +837,11 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
      * program gets its own register allocation (one kernel-wide allocation over all bodies
      * spills) and the dispatch costs one call per chunk, not per event.
      */
-    auto chunk_loop = [](size_t i) {
-        return "chunk_tiles(env, ch, ctx_all, [](const ExecEnv &e, const u64 *c, bool v, u64 x) -> u64 { return gx_body_" +
+    /* 32- and 64-byte records take the tile loop with the next tile's loads in flight */
+    auto chunk_loop = [&progs](size_t i) {
+        const uint32_t cs = progs[i]->ctx_size;
+        const std::string loop = cs == 32 ? "chunk_tiles_cw<4>" : cs == 64 ? "chunk_tiles_cw<8>" : "chunk_tiles";
+        return loop + "(env, ch, ctx_all, [](const ExecEnv &e, const u64 *c, bool v, u64 x) -> u64 { return gx_body_" +
                std::to_string(i) + "(e, c, v, x); });";
     };
     /* the stealing skeleton keeps its walk's state live across chunks: its chunk loops go out of line too */
@@ -811,16 +871,15 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
     body += ");\n}\n";
     src += "} // namespace gx\n\n";
     /*
-     * One program: a wide entry (registers as the compiler likes) and a capped one (at most
-     * 48, five 256-thread blocks per SM); the autotuner picks.  Several programs: capped
-     * only, so one heavy program does not cut every program's occupancy.
+     * One program in plain launches: four entries, from wide (two blocks per SM, up to 128
+     * registers) to capped (five blocks, 48 registers); the autotuner picks.  Persistent
+     * kernels (several programs, or a scheduling program): the wide and the capped entry,
+     * capped by default so that one heavy program does not cut every program's occupancy.
      */
-    if (progs.size() == 1) {
-        src += "extern \"C\" __global__ void __launch_bounds__(256) gx_jit_kernel(gx::ExecParams P) {\n" + body;
-        src += "extern \"C\" __global__ void __launch_bounds__(256, 5) gx_jit_kernel_capped(gx::ExecParams P) {\n" +
-               body;
-    } else {
-        src += "extern \"C\" __global__ void __launch_bounds__(256, 5) gx_jit_kernel(gx::ExecParams P) {\n" + body;
+    for (const EntrySpec &e : ENTRIES) {
+        if (!entry_built(e.variant, progs.size(), sched != nullptr)) continue;
+        src += "extern \"C\" __global__ void __launch_bounds__(256, " + std::to_string(e.min_blocks) + ") " + e.name +
+               "(gx::ExecParams P) {\n" + body;
     }
     return src;
 }
@@ -898,7 +957,7 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
         auto it = cache.find(key);
         if (it != cache.end()) {
             out.kernel = it->second.kernel;
-            out.kernel_capped = it->second.kernel_capped;
+            for (int v = 0; v < 5; v++) out.variant[v] = it->second.variant[v];
             out.key = key;
             return GX_OK;
         }
@@ -907,19 +966,23 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
     rc = jit_cubin(src, key, cubin, log);
     if (rc) return rc;
     Cached c;
-    if (cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
-        cudaLibraryGetKernel(&c.kernel, c.lib, "gx_jit_kernel") != cudaSuccess ||
-        (progs.size() == 1 && cudaLibraryGetKernel(&c.kernel_capped, c.lib, "gx_jit_kernel_capped") != cudaSuccess)) {
+    bool ok = cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) == cudaSuccess;
+    for (const EntrySpec &e : ENTRIES) {
+        if (!ok || !entry_built(e.variant, progs.size(), sched != nullptr)) continue;
+        ok = cudaLibraryGetKernel(&c.variant[e.variant], c.lib, e.name) == cudaSuccess;
+    }
+    if (!ok) {
         cudaGetLastError();
         log = "jit: loading the compiled program failed";
         return GX_E_CUDA;
     }
+    c.kernel = progs.size() == 1 && !sched ? c.variant[GX_VARIANT_4] : c.variant[GX_VARIANT_CAPPED];
     {
         std::lock_guard<std::mutex> g(cache_mu);
         cache[key] = c;
     }
     out.kernel = c.kernel;
-    out.kernel_capped = c.kernel_capped;
+    for (int v = 0; v < 5; v++) out.variant[v] = c.variant[v];
     out.key = key;
     return GX_OK;
 }
@@ -943,23 +1006,23 @@ int check_sched_program(const uint64_t *insns, uint32_t n, const gx_map_spec *ma
 }
 
 cudaError_t jit_launch(const JitKernel &k, const ExecParams &p, unsigned grid, unsigned block, size_t smem,
-                       cudaStream_t s, bool capped) {
+                       cudaStream_t s, uint32_t variant) {
     void *args[] = {(void *)&p};
-    const cudaKernel_t f = capped && k.kernel_capped ? k.kernel_capped : k.kernel;
-    return cudaLaunchKernel((const void *)f, dim3(grid), dim3(block), args, smem, s);
+    return cudaLaunchKernel((const void *)jit_entry(k, variant), dim3(grid), dim3(block), args, smem, s);
 }
 
 cudaError_t jit_set_smem(JitKernel &k, size_t bytes) {
     if (bytes <= k.smem_attr) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute((const void *)k.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess && k.kernel_capped)
-        e = cudaFuncSetAttribute((const void *)k.kernel_capped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    for (int v = 1; v < 5 && e == cudaSuccess; v++)
+        if (k.variant[v])
+            e = cudaFuncSetAttribute((const void *)k.variant[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) k.smem_attr = bytes;
     return e;
 }
 
-cudaError_t jit_occupancy(const JitKernel &k, int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)k.kernel, block, smem);
+cudaError_t jit_occupancy(const JitKernel &k, int block, size_t smem, int *blocks_per_sm, uint32_t variant) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)jit_entry(k, variant), block, smem);
 }
 
 } // namespace gx

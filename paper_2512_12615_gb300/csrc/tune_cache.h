@@ -48,7 +48,7 @@ inline bool tune_shape_valid(const gx_launch &l) {
     const bool shards_ok =
         l.shards == GX_SHARDS_OFF || ((l.shards & ~(0xFFu | GX_SHARDS_AGG)) == 0 && (w == 0 || (w >= 2 && w <= 10)));
     return l.block >= 64 && l.block <= 256 && l.block % 32 == 0 && l.ept >= 1 && l.ept <= 64 && l.reserved == 0 &&
-           l.variant <= GX_VARIANT_CAPPED && shards_ok;
+           l.variant <= GX_VARIANT_4 && shards_ok;
 }
 
 inline bool tune_cache_load(const std::string &path, gx_launch *out) {

@@ -82,13 +82,16 @@ SHARDS_AGG = 0x100  # OR into a width: warp-aggregate the updates that miss the 
 
 
 VARIANT_WIDE, VARIANT_CAPPED = 1, 2
+GRID_PER_CHUNK = 0xFFFFFFFF  # gx_launch.grid: one block per chunk of block * ept events
 
 
 def _launch(launch) -> Optional[Launch]:
-    """(block, ept[, shards[, variant]]) -> gx_launch; 0 fields mean tuned/default."""
+    """(block, ept[, shards[, variant[, grid]]]) -> gx_launch; 0 fields mean tuned/default
+    (grid 0: one wave of blocks looping over chunks; GRID_PER_CHUNK: one block per chunk)."""
     if launch is None:
         return None
-    return Launch(launch[0], launch[1], 0, launch[2] if len(launch) > 2 else 0, launch[3] if len(launch) > 3 else 0, 0)
+    return Launch(launch[0], launch[1], launch[4] if len(launch) > 4 else 0, launch[2] if len(launch) > 2 else 0,
+                  launch[3] if len(launch) > 3 else 0, 0)
 
 
 class RunStats(ctypes.Structure):
@@ -512,12 +515,14 @@ class Program:
         return st
 
     def autotune(self, events, n: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
-        """Returns the chosen (block, ept, shards); the kernel variant is in self.tuned_variant."""
+        """Returns the chosen (block, ept, shards); the kernel variant is in self.tuned_variant and
+        the grid choice (0 = one wave, GRID_PER_CHUNK) in self.tuned_grid."""
         if n is None:
             n = events.numel() * events.element_size() // self.ctx_size
         best = Launch()
         check(lib().gx_autotune(self.h, _ptr(events), n, _stream(stream), ctypes.byref(best)), "gx_autotune")
         self.tuned_variant = best.variant
+        self.tuned_grid = best.grid
         return best.block, best.ept, best.shards
 
 

@@ -54,10 +54,20 @@ def page_heat(ev: np.ndarray) -> Tuple[Dict[int, Tuple[int, int]], np.ndarray]:
 
 
 def floor_log2(x: np.ndarray) -> np.ndarray:
+    """floor(log2(x)) per element, 0 for x = 0 (count of k in 1..63 with x >> k != 0).
+    Below 2^53 every value is exact in binary64 and frexp's exponent gives the same count."""
+    x = np.asarray(x, dtype=np.uint64)
+    if x.size and int(x.max()) < (1 << 53):
+        _, e = np.frexp(x.astype(np.float64))
+        return np.maximum(e.astype(np.int64) - 1, 0)
     b = np.zeros(x.shape, dtype=np.int64)
     for k in range(1, 64):
         b += (x >> np.uint64(k)) > 0
     return b
+
+
+OUTLIER_DTYPE = np.dtype([("addr", "<u8"), ("kid", "<u4"), ("bucket", "<u4"), ("ets", "<u8"), ("xts", "<u8"),
+                          ("lat", "<u8"), ("sm", "<u4"), ("warp", "<u4")])
 
 
 def latency(ev: np.ndarray, n_kernels: int = 4096, threshold: int | None = None):
@@ -74,16 +84,37 @@ def latency(ev: np.ndarray, n_kernels: int = 4096, threshold: int | None = None)
     b = floor_log2(lat)
     idx = kid[ok].astype(np.int64) * P.LAT_BUCKETS + b[ok]
     hist = np.bincount(idx, minlength=n_kernels * P.LAT_BUCKETS).astype(np.uint64)
-    out: List[Tuple[int, bytes]] = []
-    sel = np.nonzero(ok & (lat > np.uint64(threshold)))[0]
-    for i in sel:
-        rec = np.zeros(1, dtype=[("addr", "<u8"), ("kid", "<u4"), ("bucket", "<u4"), ("ets", "<u8"), ("xts", "<u8"),
-                                 ("lat", "<u8"), ("sm", "<u4"), ("warp", "<u4")])
-        rec["addr"], rec["kid"], rec["bucket"] = e["addr"][i], kid[i], b[i]
-        rec["ets"], rec["xts"], rec["lat"] = e["ts_ns"][i], x["ts_ns"][i], lat[i]
-        rec["sm"], rec["warp"] = e["sm_id"][i], e["warp_id"][i]
-        out.append((int(i), rec.tobytes()))
+    sel, recs = latency_outliers(e, x, kid, b, lat, ok, threshold)
+    out: List[Tuple[int, bytes]] = [(int(i), recs[k].tobytes()) for k, i in enumerate(sel)]
     return hist, out
+
+
+def latency_outliers(e, x, kid, b, lat, ok, threshold):
+    """(pair indices in order, OUTLIER_DTYPE payloads) of the pairs with latency > threshold."""
+    sel = np.nonzero(ok & (lat > np.uint64(threshold)))[0]
+    recs = np.zeros(len(sel), dtype=OUTLIER_DTYPE)
+    recs["addr"], recs["kid"], recs["bucket"] = e["addr"][sel], kid[sel], b[sel]
+    recs["ets"], recs["xts"], recs["lat"] = e["ts_ns"][sel], x["ts_ns"][sel], lat[sel]
+    recs["sm"], recs["warp"] = e["sm_id"][sel], e["warp_id"][sel]
+    return sel, recs
+
+
+def latency_arrays(ev: np.ndarray, n_kernels: int = 4096, threshold: int | None = None):
+    """latency() for large batches: (hist, outlier pair indices, OUTLIER_DTYPE payloads)."""
+    if threshold is None:
+        import math
+        threshold = P.lognormal_quantile_ns(math.log(20000.0), 1.0, 0.99)
+    e, x = ev[0::2], ev[1::2]
+    kid = (e["addr"] & np.uint64(0xFFFFFFFF))
+    ok = (e["kind"] == 0) & (x["kind"] == 1) & ((x["addr"] & np.uint64(0xFFFFFFFF)) == kid)
+    ok &= kid < n_kernels
+    ok &= x["ts_ns"] >= e["ts_ns"]
+    lat = (x["ts_ns"] - e["ts_ns"])
+    b = floor_log2(lat)
+    idx = kid[ok].astype(np.int64) * P.LAT_BUCKETS + b[ok]
+    hist = np.bincount(idx, minlength=n_kernels * P.LAT_BUCKETS).astype(np.uint64)
+    sel, recs = latency_outliers(e, x, kid, b, lat, ok, threshold)
+    return hist, sel, recs
 
 
 def warp_heat(ev: np.ndarray, lanes: int = 32) -> Tuple[Dict[int, Tuple[int, int]], np.ndarray, np.ndarray]:

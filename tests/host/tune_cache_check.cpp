@@ -56,7 +56,7 @@ int main(int argc, char **argv) {
     /* refused shapes are neither stored nor loaded */
     const gx_launch bad[] = {{48, 4, 0, 0, 0, 0},   {256, 0, 0, 0, 0, 0},  {256, 65, 0, 0, 0, 0},
                              {256, 4, 0, 1, 0, 0},   {256, 4, 0, 11, 0, 0}, {256, 4, 0, 0x200, 0, 0},
-                             {256, 4, 0, 0, 3, 0},   {256, 4, 0, 0, 0, 1},  {100, 4, 0, 0, 0, 0}};
+                             {256, 4, 0, 0, 5, 0},   {256, 4, 0, 0, 0, 1},  {100, 4, 0, 0, 0, 0}};
     for (const gx_launch &b : bad) CHECK(!gx::tune_shape_valid(b) && !gx::tune_cache_store(dir + "/bad.tune", b));
     const char *garbled[] = {"", "gx-tune 2 256 8 0 8 2\n", "gx-tune 1 256 8 0\n", "gx-tune 1 48 8 0 8 2\n",
                              "gx-tune 1 256 8 0 8 2 extra\n", "tune 1 256 8 0 8 2\n", "gx-tune 1 256 8 0 8 9\n"};

@@ -135,7 +135,7 @@ def test_map_flags_are_checked(ctx):
     m.destroy()
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_kernel_variants(ctx, variant):
     """The wide and the register-capped entry of a specialised program give the same results."""
     prog, specs, cs = P.page_heat()

@@ -298,10 +298,38 @@ def test_warp_form_keeps_collectives_out_of_leader_code(tmp_path, monkeypatch):
                     assert "__syncwarp(wmask);" in tail, (f.name, line)
 
 
+def _structured_joins_are_safe(body: str, name: str) -> int:
+    """In the structured (loop-free) form the only collectives are the ballot of the valid
+    lanes, before any branch, and __syncwarp over those lanes between blocks, at the top
+    level of the body; no valid lane returns before the end.  Returns the joins seen."""
+    lines = body.splitlines()
+    start = next(i for i, l in enumerate(lines) if l.startswith("__device__ __forceinline__ u64 gx_body_"))
+    depth, joins, seen_valid_check, returns = 0, 0, False, []
+    for line in lines[start:]:
+        if "_sync(" in line or "__syncwarp" in line:
+            if line.strip() == "const u32 vm_ = __ballot_sync(0xFFFFFFFFu, valid);":
+                assert not seen_valid_check and depth == 1, (name, line)
+            else:
+                assert line.strip() == "__syncwarp(vm_);" and depth == 1, (name, line)
+                joins += 1
+        if line.strip() == "if (!valid) return 0;":
+            seen_valid_check = True
+        elif "return" in line:
+            returns.append(line.strip())
+        depth += line.count("{") - line.count("}")
+        if depth == 0:
+            break
+    # the end of the body, and the budget trip that a loop-free program never reaches
+    assert returns == ["return r0;", "return 0;"], (name, returns)
+    return joins
+
+
 def test_per_lane_form_has_no_collectives_of_its_own(tmp_path, monkeypatch):
     """Per-lane generated code runs after data-dependent branches, so a collective in it
-    could wait for lanes on another path.  It has none: warp cooperation happens inside the
-    device helpers, under the mask of the lanes that called them (__activemask())."""
+    could wait for lanes on another path.  Programs with loops have none: warp cooperation
+    happens inside the device helpers, under the mask of the lanes that called them
+    (__activemask()).  Loop-free programs join their valid lanes between basic blocks, at
+    points every valid lane passes (checked line by line)."""
     monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path))
     progs = [P.counting(), P.page_heat(), P.latency()] + [P.batch_programs()[p] for p in (0, 9, 33, 63)]
     for prog, specs, cs in progs:
@@ -309,10 +337,16 @@ def test_per_lane_form_has_no_collectives_of_its_own(tmp_path, monkeypatch):
     _check(assemble(MANY).prog(), MANY_SPECS, 32)
     sources = list(tmp_path.glob("*.cu"))
     assert len(sources) == len(progs) + 1
+    structured = 0
     for f in sources:
         body = f.read_text().split("} // namespace gx")[0]  # the program bodies, before the entry points
-        assert "_sync(" not in body, f.name
+        if "u32 nb_ = 0;" in body:
+            structured += 1
+            assert _structured_joins_are_safe(body, f.name) > 0, f.name
+        else:
+            assert "_sync(" not in body and "__syncwarp" not in body, f.name
         assert "__activemask()" in body or "agg_update" not in body, f.name
+    assert structured >= 5  # counting, latency, the generated programs; page-heat has a loop
 
 
 # ---------------------------------------------------------------- work stealing (compile only)
@@ -365,8 +399,11 @@ def test_stealing_source_shape(tmp_path, monkeypatch):
     assert text.count('#include "gx_steal.cuh"') == 1
     assert text.count("__device__ __noinline__ u64 gx_sched_call(") == 1
     assert text.count("gx::exec_steal(P,") == 2 and "gx::exec_tiles(" not in text  # wide and capped entries
-    body = text.split("__device__ __noinline__ u64 gx_sched_call(")[0].split("gx_body_1(")[1]
-    assert "_sync(" not in body
+    assert text.count("__launch_bounds__(256, 2)") == 1 and text.count("__launch_bounds__(256, 5)") == 1
+    body = "__device__ __forceinline__ u64 gx_body_1(" + text.split("__device__ __noinline__ u64 gx_sched_call(")[0].split(
+        "gx_body_1(")[1]
+    # the whole of warp 0 runs the hook (one lane valid); its only joins are the structured ones
+    assert _structured_joins_are_safe(body, src.name) > 0
     monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path / "plain"))
     _check(*P.page_heat())
     (plain,) = list((tmp_path / "plain").glob("*.cu"))
