@@ -437,9 +437,10 @@ typedef struct gx_launch {
     uint32_t variant; /* specialised programs: which compiled entry runs.  Each entry is compiled for a
                          number of resident 256-thread blocks per SM, which caps its registers per
                          thread: GX_VARIANT_WIDE 2 blocks (<= 128 registers), GX_VARIANT_CAPPED 5 (<= 48),
-                         GX_VARIANT_3 3 (<= 80), GX_VARIANT_4 4 (<= 64).  Single programs have all four;
-                         batches have WIDE and CAPPED (their default).  0 = tuned/default (GX_VARIANT_4
-                         for a single program).  Ignored by the interpreter. */
+                         GX_VARIANT_3 3 (<= 80), GX_VARIANT_4 4 (<= 64).  Programs and batches have all
+                         four (a batch steered by a scheduling program WIDE and CAPPED only).  0 =
+                         tuned/default (GX_VARIANT_4 for a single program, CAPPED for a batch).  Ignored
+                         by the interpreter. */
     uint32_t reserved;
 } gx_launch;
 #define GX_VARIANT_WIDE 1u

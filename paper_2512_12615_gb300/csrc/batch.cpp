@@ -362,7 +362,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
         uint32_t blk = lp->block ? lp->block : 256, ept = lp->ept ? lp->ept : 4;
         if (blk < 64 || blk > GX_MAX_BLOCK || blk % 32 || ept < 1 || ept > 64) return GX_EINVAL;
         if (!shards_valid(lp->shards)) return GX_EINVAL;
-        if (lp->variant != 0 && lp->variant != GX_VARIANT_WIDE && lp->variant != GX_VARIANT_CAPPED) return GX_EINVAL;
+        if (lp->variant > GX_VARIANT_4) return GX_EINVAL;
         int rc = batch_plan_shape(b, blk, ept, lp->shards, lp->variant);
         if (rc == GX_OK) b->planned = true;
         return rc;
@@ -404,9 +404,11 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
         const uint32_t blocks[] = {128, 256};
         const uint32_t epts[] = {2, 4, 8, 16};
         std::vector<uint32_t> widths = {0}; /* per-program choices ride on the chunks */
-        /* the multi-program kernel's wide and capped entries */
-        std::vector<uint32_t> variants = {0};
-        if (b->jit && b->jk.variant[GX_VARIANT_WIDE]) variants = {GX_VARIANT_CAPPED, GX_VARIANT_WIDE};
+        /* every entry the multi-program kernel has */
+        std::vector<uint32_t> variants;
+        for (uint32_t v = 1; b->jit && v < 5; v++)
+            if (b->jk.variant[v]) variants.push_back(v);
+        if (variants.empty()) variants = {0};
         for (uint32_t blk : blocks)
             for (uint32_t ept : epts) for (uint32_t w : widths) for (uint32_t v : variants) {
                 if (batch_plan_shape(b, blk, ept, w, v) != GX_OK) continue;

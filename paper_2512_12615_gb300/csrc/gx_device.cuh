@@ -121,6 +121,20 @@ __device__ __forceinline__ u64 a32(u64 dd, u64 ss) {
     return (u64)r;
 }
 
+/*
+ * Division and modulo by a register, out of line: a long instruction sequence that every
+ * site would otherwise carry.  By a constant they stay inline (a64 / a32), where the
+ * compiler turns them into multiplications.
+ */
+template <int O>
+__device__ __noinline__ u64 a64_call(u64 d, u64 s) {
+    return a64<O>(d, s);
+}
+template <int O>
+__device__ __noinline__ u64 a32_call(u64 d, u64 s) {
+    return a32<O>(d, s);
+}
+
 enum { C_EQ, C_GT, C_GE, C_SET, C_NE, C_SGT, C_SGE, C_LT, C_LE, C_SLT, C_SLE };
 
 template <int C>
@@ -232,6 +246,19 @@ __device__ __forceinline__ void agg_update(u64 addr, u64 v, u32 exec) {
     u32 grp = __match_any_sync(exec, addr);
     u64 agg = group_reduce<OP, SZ>(grp, v);
     if (lane_id() == (u32)(__ffs(grp) - 1)) plain_atomic<OP, SZ>((void *)addr, agg);
+}
+
+/*
+ * An update that goes to device memory, out of line: specialised programs with many update
+ * sites call it from each site whose block-private combining is off or missed, so a site
+ * carries a call instead of its own copy of the aggregation code (code size is what the
+ * instruction cache of a long program pays for).  agg: warp-aggregate the lanes that call
+ * together, else one atomic per lane.
+ */
+template <int OP, int SZ>
+__device__ __noinline__ void dev_update(u64 addr, u64 v, u32 agg) {
+    if (agg) agg_update<OP, SZ>(addr, v, __activemask());
+    else plain_atomic<OP, SZ>((void *)addr, v);
 }
 
 template <int OP, int SZ>
@@ -429,11 +456,17 @@ __device__ __forceinline__ u64 hash_find_word(const gx_dmap &m, u64 kw, u64 *sta
  * ordered probe above.
  */
 template <int KS, int VS>
+__device__ __noinline__ u64 hash_find_word_probe(const gx_dmap &m, u64 kw, u64 *stats) {
+    return hash_find_word<KS, VS>(m, kw, stats);
+}
+
+/* OUTLINE: the ordered probe out of line (programs with many lookup sites) */
+template <int KS, int VS, bool OUTLINE = false>
 __device__ __forceinline__ u64 hash_find_word_nd(const gx_dmap &m, u64 kw, u64 *stats) {
     const u64 i = mix64(0x9E3779B97F4A7C15ull ^ (u64)KS ^ kw) & m.mask;
     const ulonglong2 v = *(const ulonglong2 *)(m.slots + i * 16u);
     if ((u32)v.x == GX_SLOT_FULL && v.y == kw && kw != 0) return (u64)(m.values + i * (u64)VS);
-    return hash_find_word<KS, VS>(m, kw, stats);
+    return OUTLINE ? hash_find_word_probe<KS, VS>(m, kw, stats) : hash_find_word<KS, VS>(m, kw, stats);
 }
 
 /* lookup with lanes that look up the same (<= 8 byte) key sharing one probe */
@@ -772,53 +805,53 @@ template <typename RunChunk, typename Init, typename Flush>
 __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunChunk run_chunk, Init wc_init, Flush wc_flush) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ u32 s_chunk;
-    __shared__ const uint8_t *s_image;
     u64 *ctx_all = (u64 *)(smem + P.image_area);
-    if (P.mode == 0) {
-        /* chunks of blockDim * ept events; block b runs chunks b, b + gridDim, ... with the
-           image staged and the combining area open once for all of them */
-        stage_image(smem, P.image, P.image_bytes);
-        const ExecEnv env = stage_env(smem, P, 0, P.wc_bits);
-        if (env.wc_bits) {
-            wc_init(env);
-            __syncthreads();
-        }
-        const u64 per = (u64)blockDim.x * P.ept;
-        gx_chunk ch;
-        ch.image = P.image;
-        ch.events = P.events;
-        ch.ret_out = P.ret_out;
-        ch.idx_base = P.idx_base;
-        ch.image_bytes = P.image_bytes;
-        ch.ctx_size = P.ctx_size;
-        ch.pad = 0;
-        for (u64 b = (u64)blockIdx.x * per; b < P.n; b += (u64)gridDim.x * per) {
-            ch.begin = b;
-            ch.end = b + per < P.n ? b + per : P.n;
-            run_chunk(env, ch, ctx_all);
-        }
-        if (env.wc_bits) {
-            __syncthreads();
-            wc_flush(env);
-        }
-        return;
-    }
-    const u32 nchunks = P.nchunks_dev ? *P.nchunks_dev : P.nchunks;
-    if (threadIdx.x == 0) s_image = nullptr;
+    /*
+     * One loop for both modes, so the per-event code is inlined once.  Plain: chunks of
+     * blockDim * ept events, block b taking the chunks that start at b, b + gridDim, ...
+     * of one program.  Persistent: chunks claimed from the table.  Every decision below is
+     * block-uniform (plain: this block's position; persistent: the claimed chunk in shared
+     * memory), so the barriers inside are reached by every thread.
+     */
+    const bool plain = P.mode == 0;
+    const u64 per = (u64)blockDim.x * P.ept;
+    const u32 nchunks = plain ? 0u : (P.nchunks_dev ? *P.nchunks_dev : P.nchunks);
+    u64 next = (u64)blockIdx.x * per; /* plain: the first event of this block's next chunk */
+    const uint8_t *staged = nullptr;  /* the image in shared memory */
     ExecEnv open;
     u32 open_wcp = 0;
-    bool is_open = false; /* block-uniform */
+    bool is_open = false;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_chunk = atomicAdd(P.cursor, 1u);
-        __syncthreads();
-        const u32 c = s_chunk;
-        const bool done = c >= nchunks;
         gx_chunk ch;
         u32 wcp = 0;
-        if (!done) {
-            ch = P.chunks[c];
-            wcp = (ch.pad >> 63) ? (u32)(ch.pad >> 32) & 0x1FFu : P.wc_bits; /* the chunk's own choice */
+        bool done;
+        if (plain) {
+            done = next >= P.n;
+            if (!done) {
+                ch.image = P.image;
+                ch.events = P.events;
+                ch.ret_out = P.ret_out;
+                ch.begin = next;
+                ch.end = next + per < P.n ? next + per : P.n;
+                ch.idx_base = P.idx_base;
+                ch.image_bytes = P.image_bytes;
+                ch.ctx_size = P.ctx_size;
+                ch.pad = 0;
+                wcp = P.wc_bits;
+                next += (u64)gridDim.x * per;
+            } else if (is_open) {
+                __syncthreads(); /* every warp is done with its last tile before the flush */
+            }
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) s_chunk = atomicAdd(P.cursor, 1u);
+            __syncthreads();
+            const u32 c = s_chunk;
+            done = c >= nchunks;
+            if (!done) {
+                ch = P.chunks[c];
+                wcp = (ch.pad >> 63) ? (u32)(ch.pad >> 32) & 0x1FFu : P.wc_bits; /* the chunk's own choice */
+            }
         }
         if (is_open && (done || (u32)ch.pad != open.slot || wcp != open_wcp)) {
             wc_flush(open);
@@ -826,9 +859,9 @@ __device__ __forceinline__ void exec_tiles(const ExecParams &P, RunChunk run_chu
             is_open = false;
         }
         if (done) break;
-        if (ch.image != s_image) {
+        if (ch.image != staged) {
             stage_image(smem, ch.image, ch.image_bytes);
-            if (threadIdx.x == 0) s_image = ch.image;
+            staged = ch.image;
         }
         const ExecEnv env = stage_env(smem, P, (u32)ch.pad, wcp);
         if (env.wc_bits && !is_open) {

@@ -300,11 +300,15 @@ std::string gen_wc_flush(const ShardPlan &sp, int slot) {
     return o.str();
 }
 
+/* a program with more map-update and lookup sites than this calls their slow paths out of line */
+const uint32_t OUTLINE_SITES = 8;
+
 /* an update of map memory at `addr` by `val`: combined per block when the plan allows */
 std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, int size, const std::string &addr,
-                       const std::string &val) {
-    std::string global = std::string("agg_update<") + op + ", " + std::to_string(size) + ">(" + addr + ", " + val +
-                         ", __activemask());";
+                       const std::string &val, bool outline) {
+    const std::string t0 = std::string("<") + op + ", " + std::to_string(size) + ">";
+    std::string global = outline ? "dev_update" + t0 + "(" + addr + ", " + val + ", 1u);"
+                                 : "agg_update" + t0 + "(" + addr + ", " + val + ", __activemask());";
     const ShardMap *sm = ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES ? sp.find(ii.vmap) : nullptr;
     if (!sm) return global;
     const size_t k = (size_t)(sm - sp.maps.data());
@@ -317,9 +321,12 @@ std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, 
     } else {
         o << "uint8_t *e_ = wc_entry(env.shard + " << cache_off(sp, k) << ", " << cache_bits(*sm) << ", "
           << 8 + sm->stride << "u, a_ - " << ii.voff << "ull); "
-          << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); "
-          << "else if (env.wc_agg) agg_update" << t << "(a_, " << val << ", __activemask()); "
-          << "else plain_atomic" << t << "((void *)a_, " << val << "); ";
+          << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); ";
+        if (outline)
+            o << "else dev_update" << t << "(a_, " << val << ", env.wc_agg); ";
+        else
+            o << "else if (env.wc_agg) agg_update" << t << "(a_, " << val << ", __activemask()); "
+              << "else plain_atomic" << t << "((void *)a_, " << val << "); ";
     }
     o << "} else " << global;
     return o.str();
@@ -394,6 +401,27 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
      * warp-level handlers (whose lanes never diverge).
      */
     const bool structured = acyclic && !p.warp;
+    /*
+     * Many map-update and lookup sites: their slow paths (device-memory updates, the
+     * ordered hash probe) go out of line, so that a long program's code fits the
+     * instruction cache; a few sites keep them inline and save the call.
+     */
+    uint32_t sites = 0;
+    for (uint32_t pc = 0; pc < n; pc++) {
+        if (!p.info[pc].visited) continue;
+        const uint64_t w = p.insns[pc];
+        const int op = (int)(w & 0xFF);
+        const int32_t imm = (int32_t)(uint32_t)(w >> 32);
+        if (op == 0x18) {
+            pc++;
+            continue;
+        }
+        if ((op & 0x07) == 3 && (op & 0xE0) == 0xC0 && p.info[pc].kind != MK_STACK) sites++;
+        if (op == 0x85 && (imm == GX_HELPER_MAP_LOOKUP || imm == GX_HELPER_ATOMIC_MAX_U64 ||
+                           imm == GX_HELPER_ATOMIC_MIN_U64))
+            sites++;
+    }
+    const bool outline = sites > OUTLINE_SITES;
     /* scalar stack unless some load / store / atomic reaches the stack at a varying offset */
     bool scalar = true;
     for (uint32_t pc = 0; pc < n; pc++)
@@ -497,8 +525,11 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                 return GX_EINVAL;
             }
             std::string s = x ? R(src) : (w32 ? hex64((uint32_t)imm) : hex64((uint64_t)(int64_t)imm));
+            const bool call = x && (code == 0x30 || code == 0x90); /* division by a register: out of line */
             if (code == 0xB0 && !w32) o << d << " = " << s << ";";
-            else o << d << " = " << (w32 ? "a32<" : "a64<") << oname << ">(" << d << ", " << s << ");";
+            else
+                o << d << " = " << (w32 ? (call ? "a32_call<" : "a32<") : (call ? "a64_call<" : "a64<")) << oname << ">("
+                  << d << ", " << s << ");";
             break;
         }
         case 5: case 6: {
@@ -550,7 +581,8 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     } else if (inline_lookup) {
                         const std::string ks = std::to_string(ms->key_size);
                         o << "r0 = hash_find_word" << ((ms->flags & GX_MAP_F_NO_DELETE) ? "_nd<" : "<") << ks << ", "
-                          << vs << ">(" << m << ", " << key(ms->key_size) << ", env.stats);";
+                          << vs << ((ms->flags & GX_MAP_F_NO_DELETE) && outline ? ", true" : "") << ">(" << m << ", "
+                          << key(ms->key_size) << ", env.stats);";
                     } else {
                         o << "r0 = map_lookup(" << m << ", (const uint8_t *)r2, __activemask(), env.stats);";
                     }
@@ -578,10 +610,10 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     o << "((u32 *)(r1 - GX_RB_HDR))[1] = GX_RB_DISCARDED;";
                     break;
                 case GX_HELPER_ATOMIC_MAX_U64:
-                    o << gen_update(sp, ii, "AG_MAX", 8, "r1", "r2");
+                    o << gen_update(sp, ii, "AG_MAX", 8, "r1", "r2", outline);
                     break;
                 case GX_HELPER_ATOMIC_MIN_U64:
-                    o << gen_update(sp, ii, "AG_MIN", 8, "r1", "r2");
+                    o << gen_update(sp, ii, "AG_MIN", 8, "r1", "r2", outline);
                     break;
                 default: log = "jit: unknown helper"; return GX_EINVAL;
                 }
@@ -678,7 +710,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
                     const char *ag = b == 0x00 ? "AG_ADD" : b == 0x40 ? "AG_OR" : b == 0x50 ? "AG_AND" : "AG_XOR";
                     if (imm & 1) o << R(src) << " = fetch_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ");";
                     else if (ii.kind == MK_STACK) o << "agg_update<" << ag << ", " << sz << ">(" << addr << ", " << R(src) << ", __activemask());";
-                    else o << gen_update(sp, ii, ag, size, addr, R(src));
+                    else o << gen_update(sp, ii, ag, size, addr, R(src), outline);
                 }
                 close();
                 break;
@@ -734,9 +766,10 @@ const EntrySpec ENTRIES[] = {{GX_VARIANT_WIDE, "gx_jit_kernel", 2},
                              {GX_VARIANT_3, "gx_jit_kernel_v3", 3},
                              {GX_VARIANT_4, "gx_jit_kernel_v4", 4}};
 
-/* plain single programs get every entry; persistent kernels the wide and the capped one */
+/* every kernel gets the four entries, except work-stealing ones (the wide and the capped) */
 bool entry_built(uint32_t variant, size_t n_progs, bool sched) {
-    return (n_progs == 1 && !sched) || variant == GX_VARIANT_WIDE || variant == GX_VARIANT_CAPPED;
+    (void)n_progs;
+    return !sched || variant == GX_VARIANT_WIDE || variant == GX_VARIANT_CAPPED;
 }
 std::mutex cache_mu;
 std::map<std::string, Cached> cache;
@@ -871,10 +904,10 @@ std::string jit_source(const std::vector<const JitProgram *> &progs, std::string
     body += ");\n}\n";
     src += "} // namespace gx\n\n";
     /*
-     * One program in plain launches: four entries, from wide (two blocks per SM, up to 128
-     * registers) to capped (five blocks, 48 registers); the autotuner picks.  Persistent
-     * kernels (several programs, or a scheduling program): the wide and the capped entry,
-     * capped by default so that one heavy program does not cut every program's occupancy.
+     * Four entries, from wide (two blocks per SM, up to 128 registers) to capped (five
+     * blocks, 48 registers); the autotuner picks.  A kernel of several programs defaults to
+     * the capped entry, so that one heavy program does not cut every program's occupancy;
+     * a work-stealing kernel has the wide and the capped entry only.
      */
     for (const EntrySpec &e : ENTRIES) {
         if (!entry_built(e.variant, progs.size(), sched != nullptr)) continue;
