@@ -542,7 +542,12 @@ int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_
  * started.  A cancelled block never runs, so every chunk still runs exactly once; a cancel
  * whose response does not come within the wait bound ends that block's stealing and sets
  * the scheduling program's status to GX_E_TIMEOUT (the chunk it may have cancelled is then
- * lost).  Tallies are per launched block; cancelled blocks' rows stay zero.
+ * lost).  The block waits once more, bounded, for the response before it exits; should
+ * that wait end too, the response may still land in the shared memory of a later block on
+ * that SM.  So once gx_last_status of a scheduling program under launch control has
+ * reported GX_E_TIMEOUT, launch control is refused on the context for good:
+ * gx_batch_set_sched with this flag and gx_batch_launch of such a batch return
+ * GX_E_TIMEOUT.  Tallies are per launched block; cancelled blocks' rows stay zero.
  */
 #define GX_SCHED_F_LAUNCH_CONTROL 1u
 /*

@@ -844,6 +844,7 @@ int gx_last_status(gx_prog *p, gx_run_stats *out, int reset, void *stream) {
     if (cudaMemcpy(st, p->dstats, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return GX_E_CUDA;
     memset(out, 0, sizeof *out);
     out->status = (int32_t)(uint32_t)st[GX_STAT_STATUS];
+    if (out->status == GX_E_TIMEOUT && p->sched_lc) p->ctx->launch_control_timed_out = true;
     out->budget_trips = st[GX_STAT_BUDGET];
     out->waits_expired = st[GX_STAT_WAITS];
     out->launches = p->launches;

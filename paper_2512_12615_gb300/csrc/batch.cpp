@@ -441,6 +441,7 @@ int gx_batch_plan(gx_batch *b, const gx_launch *lp, void *stream) {
 
 int gx_batch_launch(gx_batch *b, void *stream) {
     if (!b || !b->planned) return GX_EINVAL;
+    if (b->persist.launch_control && b->ctx->launch_control_timed_out) return GX_E_TIMEOUT;
     TraceRange tr("gx_batch_launch");
     int rc = b->persist.launch((cudaStream_t)stream);
     if (rc == GX_OK) {
@@ -464,9 +465,11 @@ int gx_batch_set_sched(gx_batch *b, gx_prog *hook, uint64_t budget_ns, const gx_
         log[k] = 0;
     }
     if (rc) return rc;
+    if ((flags & GX_SCHED_F_LAUNCH_CONTROL) && b->ctx->launch_control_timed_out) return GX_E_TIMEOUT;
     b->sched = hook;
     b->sched_budget = budget_ns;
     b->sched_flags = flags;
+    if (flags & GX_SCHED_F_LAUNCH_CONTROL) hook->sched_lc = true;
     return GX_OK;
 }
 

@@ -16,7 +16,7 @@
 namespace gx {
 namespace {
 
-uint32_t H(int fam, int reg) { return (uint32_t)(fam * 16 + reg); }
+uint32_t H(int fam, int reg) { return (uint32_t)(fam * GX_HSTRIDE + reg); }
 uint32_t S(int single) { return (uint32_t)(GX_SINGLE_BASE + single); }
 int size_index(int size) { return size == 1 ? 0 : size == 2 ? 1 : size == 4 ? 2 : 3; }
 int size_of(int op) { return (op & 0x18) == 0x00 ? 4 : (op & 0x18) == 0x08 ? 2 : (op & 0x18) == 0x10 ? 1 : 8; }

@@ -8,7 +8,7 @@
  * register file at run time.  Operands that would need a second register go through two
  * temporaries: T (second operand / value) and B (memory base address).
  *
- *   bits  0..15  handler id  = family * 16 + register   (families below)
+ *   bits  0..15  handler id  = family * 11 + register   (families below)
  *                             or GX_SINGLE_BASE + k      (register-free handlers)
  *   bits 16..31  aux         jump target (micro-op index), or absolute ctx / stack offset
  *   bits 32..63  imm         signed 32-bit immediate / memory offset
@@ -24,7 +24,7 @@
 #endif
 
 /*
- * Register-specialised families: the handler id carries the eBPF register (16 slots per
+ * Register-specialised families: the handler id carries the eBPF register (11 slots per
  * family; R0..R9, plus R10 for the three temp loads MOVT/MOVA/MOVB).  Rare operations
  * are "singles" that work on the temporaries only: A (accumulator), T (operand),
  * B (base address); the decoder wraps them in MOVA/MOVT and MOVRA/MOVR.
@@ -63,7 +63,10 @@
 
 #define GX_ENUM_FAM(n) GXF_##n,
 enum gx_family { GX_FAMILIES(GX_ENUM_FAM) GX_NUM_FAMILIES };
-#define GX_SINGLE_BASE (GX_NUM_FAMILIES * 16)
+/* handler ids are dense (family * 11 + register), so the interpreter's dispatch is one
+   indexed jump over contiguous cases rather than a search */
+#define GX_HSTRIDE 11
+#define GX_SINGLE_BASE (GX_NUM_FAMILIES * GX_HSTRIDE)
 #define GX_ENUM_SINGLE(n) GXS_##n,
 enum gx_single { GX_SINGLES(GX_ENUM_SINGLE) GX_NUM_SINGLES };
 #define GX_NUM_HANDLERS (GX_SINGLE_BASE + GX_NUM_SINGLES)

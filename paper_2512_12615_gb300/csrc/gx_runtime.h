@@ -29,6 +29,10 @@ struct gx_ctx {
     uint64_t l2_bytes = 0;
     std::atomic<int> live{0};
     std::mutex mu;
+    /* a cancel response of cluster launch control did not arrive in time: launch control
+       stays refused on this context (a late response may still land in a block's shared
+       memory, so the results of that launch and of its SMs' later blocks are suspect) */
+    std::atomic<bool> launch_control_timed_out{false};
 };
 
 struct gx_map {
@@ -55,6 +59,7 @@ struct gx_prog {
     uint64_t launches = 0;
     std::map<int, gx_launch> tuned; /* log2(n) bucket -> shape */
     std::map<uint64_t, int> occupancy; /* (block, shared bytes, variant) -> resident blocks per SM */
+    bool sched_lc = false; /* steers a batch under cluster launch control (gx_batch_set_sched) */
     uint32_t pref_shards = 0;       /* tuned gx_launch.shards of this program in batches and ticks */
     bool pref_tuned = false;
     /* load-time specialisation (GX_PROG_JIT) */

@@ -38,17 +38,17 @@ namespace gx {
 
 /* handler-case generators: one case per eBPF register */
 #define RC10(FAM, M, A, B)                                                                  \
-    case (FAM)*16 + 0: { M(r0, A, B) } break;                                               \
-    case (FAM)*16 + 1: { M(r1, A, B) } break;                                               \
-    case (FAM)*16 + 2: { M(r2, A, B) } break;                                               \
-    case (FAM)*16 + 3: { M(r3, A, B) } break;                                               \
-    case (FAM)*16 + 4: { M(r4, A, B) } break;                                               \
-    case (FAM)*16 + 5: { M(r5, A, B) } break;                                               \
-    case (FAM)*16 + 6: { M(r6, A, B) } break;                                               \
-    case (FAM)*16 + 7: { M(r7, A, B) } break;                                               \
-    case (FAM)*16 + 8: { M(r8, A, B) } break;                                               \
-    case (FAM)*16 + 9: { M(r9, A, B) } break;
-#define RC11(FAM, M, A, B) RC10(FAM, M, A, B) case (FAM)*16 + 10: { M(r10, A, B) } break;
+    case (FAM)*GX_HSTRIDE + 0: { M(r0, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 1: { M(r1, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 2: { M(r2, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 3: { M(r3, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 4: { M(r4, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 5: { M(r5, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 6: { M(r6, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 7: { M(r7, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 8: { M(r8, A, B) } break;                                               \
+    case (FAM)*GX_HSTRIDE + 9: { M(r9, A, B) } break;
+#define RC11(FAM, M, A, B) RC10(FAM, M, A, B) case (FAM)*GX_HSTRIDE + 10: { M(r10, A, B) } break;
 
 #define IMM ((int32_t)(u >> 32))
 #define AUX ((u32)(u >> 16) & 0xFFFFu)

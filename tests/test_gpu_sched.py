@@ -3,9 +3,7 @@ shares of the chunk table and a `should_try_steal` program (FixedWork, Greedy,
 LatencyBudget; Sec. 4.3.2, Sec. 6) decides, before each chunk a block would take from
 another share, whether it takes it.
 
-These tests are marked `gpu_pending`, not `gpu`: the kernel has not yet run on a GPU, so
-they are selected only explicitly (`pytest -m gpu_pending`) and skip without one.  What
-they hold it to:
+What they hold it to:
   - the items' maps and R0 equal the oracle's, whatever the policy (every chunk runs once);
   - the per-block tallies: owned + stolen summed = the chunk count; FixedWork, and
     LatencyBudget with a zero budget, leave each block exactly its share;
@@ -17,8 +15,8 @@ they hold it to:
     cancelled blocks leave zero rows, every other block ran its own chunk.
 The walk itself (exactly-once under any interleaving) is pinned on the host
 (tests/test_host_steal.py); the kernel compiles on the host (tests/test_jit_compile.py).
-Run `-k first_run` alone first: one small item, FixedWork (then Greedy under launch control,
-the first run of its cancel and bounded mbarrier wait).
+The `first_run` cases are the smallest: one small item, FixedWork (then Greedy under launch
+control, the first use of its cancel and bounded mbarrier wait).
 """
 import numpy as np
 import pytest
@@ -28,7 +26,7 @@ from tests.asmtext import assemble
 from workloads import gen
 from workloads import programs as P
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no GPU", allow_module_level=True)

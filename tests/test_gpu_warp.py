@@ -1,16 +1,15 @@
 """The warp-level form (gx_verify_load_simt) against the oracle's warp run, bit for bit.
 
-These tests are marked `gpu_pending`, not `gpu`: the form has not yet run on a GPU, so
-they are selected only explicitly (`pytest -m gpu_pending`) and skip without one.  They
-cover warp_heat over warp-context records with planted bad warps, misaligned lanes and a
-ragged last warp; random SIMT handlers accepted in deterministic mode; one warp of the
-program with every shared effect; several launch shapes and combining widths; and the
-refusals (no interpreter form; a batch that would interpret it).
+They cover warp_heat over warp-context records with planted bad warps, misaligned lanes
+and a ragged last warp; random SIMT handlers accepted in deterministic mode; one warp of
+the program with every shared effect; several launch shapes and combining widths; and
+the refusals (no interpreter form; a batch that would interpret it).
 
-Before the first run: the generated form puts leader-only code with loops before a
-__shfl_sync, the shape suspected in the one hang this engine's specialisation caused.
-Settle that by reading first, then run the smallest cases alone under a short time limit
-(`-m gpu_pending -k first_run`, which run one warp before anything larger).
+The generated form puts leader-only code (helper calls with bounded probe loops) inside
+`if (lead)`, then joins the warp's valid lanes with __syncwarp and broadcasts.  Every lane
+of that mask reaches every join: the mask is taken at entry, SIMT verification makes each
+branch uniform across the valid lanes, and exits and budget trips are uniform too.  The
+`first_run` cases are the smallest (one warp), for a first run on new hardware.
 """
 import numpy as np
 import pytest
@@ -20,7 +19,7 @@ from tests.asmtext import assemble
 from workloads import gen
 from workloads import programs as P
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no GPU", allow_module_level=True)
