@@ -757,7 +757,7 @@ int gx_verify_load_simt(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *co
     return GX_OK;
 }
 
-uint32_t gx_prog_uops(const gx_prog *p) { return p ? (uint32_t)p->uops.size() : 0; }
+uint32_t gx_prog_uops(const gx_prog *p) { return p ? (uint32_t)(p->uops.size() / 2) : 0; } /* two words each */
 
 /* ---------------------------------------------------------------- runs */
 int gx_run_batch_ex(gx_prog *p, const void *events, uint64_t n, uint64_t idx_base, int64_t *ret_out,

@@ -1,20 +1,19 @@
 /*
  * Layouts shared by the host side (decoder, map management) and the device kernels.
  *
- * Decoded program ("micro-ops").  The verifier annotates every instruction with the
- * memory region it touches; the decoder then turns each eBPF instruction into one or
- * two 64-bit micro-ops whose handler is specialised on the eBPF register it writes (or
- * reads), so the interpreter keeps R0..R10 in GPU registers and never indexes a
- * register file at run time.  Operands that would need a second register go through two
- * temporaries: T (second operand / value) and B (memory base address).
- *
- *   bits  0..15  handler id  = family * 11 + register   (families below)
- *                             or GX_SINGLE_BASE + k      (register-free handlers)
- *   bits 16..31  aux         jump target (micro-op index), or absolute ctx / stack offset
- *   bits 32..63  imm         signed 32-bit immediate / memory offset
+ * Decoded program ("micro-ops"): one 16-byte micro-op per eBPF instruction (the second
+ * slot of a 64-bit immediate becomes a NOP).  The verifier annotates every instruction
+ * with the memory region it touches, so ctx and stack accesses carry their proven
+ * absolute offsets and map / ring-buffer accesses their region.  The interpreter keeps
+ * R0..R10 in a per-thread array indexed by the dst / src fields.
+ *   word 0  bits  0..7   operation (enum gx_op)
+ *           bits  8..11  dst register, bits 12..15 src register
+ *           bits 16..31  aux: jump target (micro-op index), or absolute ctx / stack offset
+ *           bits 32..63  imm: signed 32-bit immediate, or memory offset
+ *   word 1  the 64-bit value of a 64-bit immediate (map references: the map's index)
  *
  * Device program image (16-byte aligned, staged whole into shared memory):
- *   gx_dprog_hdr | gx_dmap[n_maps] | u64 uops[n_uops]
+ *   gx_dprog_hdr | gx_dmap[n_maps] | u64 uops[2 * n_uops]
  */
 #ifndef GX_LAYOUT_H
 #define GX_LAYOUT_H
@@ -24,56 +23,41 @@
 #endif
 
 /*
- * Register-specialised families: the handler id carries the eBPF register (11 slots per
- * family; R0..R9, plus R10 for the three temp loads MOVT/MOVA/MOVB).  Rare operations
- * are "singles" that work on the temporaries only: A (accumulator), T (operand),
- * B (base address); the decoder wraps them in MOVA/MOVT and MOVRA/MOVR.
+ * Operations.  ALU: width (64, 32) x operand (K immediate, X register) x the 14 RFC 9669
+ * operations, in enum order (O_ADD .. O_MOV of the device header); jumps: the 11
+ * conditions x (64 K, 64 X, 32 K, 32 X); loads: region (C ctx, S stack, M memory) x size
+ * (1, 2, 4, 8, then sign-extending 1, 2, 4); stores: region (S, M) x size, immediate or
+ * register; atomics: region (S, M) x the 20 forms; then the helper calls.
  */
-#define GX_FAST_ALU(X, W, F) \
-    X(ADD##W##F) X(SUB##W##F) X(MUL##W##F) X(OR##W##F) X(AND##W##F) X(XOR##W##F) X(LSH##W##F) X(RSH##W##F) \
-    X(MOV##W##F)
-#define GX_FAST_JMP(X, W, F) \
-    X(JEQ##W##F) X(JNE##W##F) X(JGT##W##F) X(JGE##W##F) X(JLT##W##F) X(JLE##W##F) X(JSGT##W##F) X(JSGE##W##F) \
-    X(JSLT##W##F) X(JSLE##W##F) X(JSET##W##F)
+#define GX_ALU_OPS(X, P) X(P##ADD) X(P##SUB) X(P##MUL) X(P##DIV) X(P##SDIV) X(P##MOD) X(P##SMOD) \
+    X(P##OR) X(P##AND) X(P##XOR) X(P##LSH) X(P##RSH) X(P##ARSH) X(P##MOV)
+#define GX_JMP_OPS(X, P) X(P##JEQ) X(P##JNE) X(P##JGT) X(P##JGE) X(P##JLT) X(P##JLE) X(P##JSGT) \
+    X(P##JSGE) X(P##JSLT) X(P##JSLE) X(P##JSET)
+#define GX_LD_OPS(X, P) X(P##1) X(P##2) X(P##4) X(P##8) X(P##S1) X(P##S2) X(P##S4)
+#define GX_SZ_OPS(X, P) X(P##1) X(P##2) X(P##4) X(P##8)
+#define GX_ATOM_OPS(X, P) X(P##ADD4) X(P##OR4) X(P##AND4) X(P##XOR4) X(P##ADD8) X(P##OR8) X(P##AND8) \
+    X(P##XOR8) X(P##FADD4) X(P##FOR4) X(P##FAND4) X(P##FXOR4) X(P##FADD8) X(P##FOR8) X(P##FAND8) \
+    X(P##FXOR8) X(P##XCHG4) X(P##XCHG8) X(P##CMPX4) X(P##CMPX8)
 
-#define GX_FAMILIES(X)                                                                           \
-    X(MOVT) X(MOVA) X(MOVB) X(MOVR) X(MOVRA) X(LDIMM64)                                          \
-    GX_FAST_ALU(X, 64, K) GX_FAST_ALU(X, 64, T) GX_FAST_ALU(X, 32, K) GX_FAST_ALU(X, 32, T)      \
-    GX_FAST_JMP(X, 64, K) GX_FAST_JMP(X, 64, T) GX_FAST_JMP(X, 32, K)                            \
-    X(LDXC1) X(LDXC2) X(LDXC4) X(LDXC8) X(LDXCS1) X(LDXCS2) X(LDXCS4)                            \
-    X(LDXS1) X(LDXS2) X(LDXS4) X(LDXS8) X(LDXSS1) X(LDXSS2) X(LDXSS4)                            \
-    X(LDXM1) X(LDXM2) X(LDXM4) X(LDXM8) X(LDXMS1) X(LDXMS2) X(LDXMS4)                            \
-    X(STXS1) X(STXS2) X(STXS4) X(STXS8)
-
-#define GX_SLOW_ALU(X, W, F) X(DIV##W##F) X(SDIV##W##F) X(MOD##W##F) X(SMOD##W##F) X(ARSH##W##F)
-
-#define GX_SINGLES(X)                                                                            \
-    GX_SLOW_ALU(X, 64, K) GX_SLOW_ALU(X, 64, T) GX_SLOW_ALU(X, 32, K) GX_SLOW_ALU(X, 32, T)      \
+#define GX_OPS(X)                                                                                \
+    GX_ALU_OPS(X, A64K_) GX_ALU_OPS(X, A64X_) GX_ALU_OPS(X, A32K_) GX_ALU_OPS(X, A32X_)          \
     X(NEG64) X(NEG32) X(MOVSX64_8) X(MOVSX64_16) X(MOVSX64_32) X(MOVSX32_8) X(MOVSX32_16)        \
-    X(LE16) X(LE32) X(BSWAP16) X(BSWAP32) X(BSWAP64)                                             \
-    GX_FAST_JMP(X, 32, A)                                                                        \
-    X(ST_S1) X(ST_S2) X(ST_S4) X(ST_S8) X(ST_M1) X(ST_M2) X(ST_M4) X(ST_M8)                      \
-    X(STT_S1) X(STT_S2) X(STT_S4) X(STT_S8) X(STT_M1) X(STT_M2) X(STT_M4) X(STT_M8)              \
-    X(AADD4) X(AOR4) X(AAND4) X(AXOR4) X(AADD8) X(AOR8) X(AAND8) X(AXOR8)                        \
-    X(AFADD4) X(AFOR4) X(AFAND4) X(AFXOR4) X(AFADD8) X(AFOR8) X(AFAND8) X(AFXOR8)                \
-    X(AXCHG4) X(AXCHG8) X(ACMPX4) X(ACMPX8)                                                      \
-    X(JA) X(EXIT) X(NOP) X(MOVB_STK)                                                             \
+    X(LE16) X(LE32) X(BSWAP16) X(BSWAP32) X(BSWAP64) X(LDIMM64)                                   \
+    GX_JMP_OPS(X, J64K_) GX_JMP_OPS(X, J64X_) GX_JMP_OPS(X, J32K_) GX_JMP_OPS(X, J32X_)          \
+    X(JA) X(EXIT) X(NOP)                                                                         \
+    GX_LD_OPS(X, LDC) GX_LD_OPS(X, LDS) GX_LD_OPS(X, LDM)                                        \
+    GX_SZ_OPS(X, STIS) GX_SZ_OPS(X, STIM) GX_SZ_OPS(X, STXS) GX_SZ_OPS(X, STXM)                  \
+    GX_ATOM_OPS(X, AS_) GX_ATOM_OPS(X, AM_)                                                      \
     X(CALL_LOOKUP) X(CALL_UPDATE) X(CALL_DELETE) X(CALL_RB_OUTPUT) X(CALL_RB_RESERVE)             \
     X(CALL_RB_SUBMIT) X(CALL_RB_DISCARD) X(CALL_AMAX) X(CALL_AMIN)
 
-#define GX_ENUM_FAM(n) GXF_##n,
-enum gx_family { GX_FAMILIES(GX_ENUM_FAM) GX_NUM_FAMILIES };
-/* handler ids are dense (family * 11 + register), so the interpreter's dispatch is one
-   indexed jump over contiguous cases rather than a search */
-#define GX_HSTRIDE 11
-#define GX_SINGLE_BASE (GX_NUM_FAMILIES * GX_HSTRIDE)
-#define GX_ENUM_SINGLE(n) GXS_##n,
-enum gx_single { GX_SINGLES(GX_ENUM_SINGLE) GX_NUM_SINGLES };
-#define GX_NUM_HANDLERS (GX_SINGLE_BASE + GX_NUM_SINGLES)
+#define GX_ENUM_OP(n) GXO_##n,
+enum gx_op { GX_OPS(GX_ENUM_OP) GX_NUM_OPS };
 
 #ifndef __CUDACC_RTC__
-static inline uint64_t gx_uop(uint32_t handler, uint32_t aux, int32_t imm) {
-    return (uint64_t)(handler & 0xFFFFu) | ((uint64_t)(aux & 0xFFFFu) << 16) | ((uint64_t)(uint32_t)imm << 32);
+static inline uint64_t gx_uop(uint32_t op, uint32_t dst, uint32_t src, uint32_t aux, int32_t imm) {
+    return (uint64_t)(op & 0xFFu) | ((uint64_t)(dst & 0xFu) << 8) | ((uint64_t)(src & 0xFu) << 12) |
+           ((uint64_t)(aux & 0xFFFFu) << 16) | ((uint64_t)(uint32_t)imm << 32);
 }
 #endif
 

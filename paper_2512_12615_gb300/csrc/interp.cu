@@ -8,8 +8,9 @@
  *   - the 32-byte (or ctx_size-byte) records of a warp are read with coalesced 16-byte
  *     streaming loads and transposed into shared memory, so ctx field loads are
  *     bank-conflict free;
- *   - R0..R10 live in GPU registers: every micro-op handler is specialised on the
- *     register it touches (see gx_layout.h), the dispatch index is warp-uniform;
+ *   - one 16-byte micro-op per eBPF instruction, dispatched on a dense operation id
+ *     (warp-uniform while the lanes agree); R0..R10 in a per-thread array indexed by
+ *     the micro-op's register fields (local memory, held in L1);
  *   - divergence: while all 32 lanes sit at the same pc the warp runs in uniform mode;
  *     after a split branch it runs "min-pc" mode (only lanes at the smallest pc
  *     advance), which re-converges forward-branching code at its join points;
@@ -36,89 +37,83 @@ namespace gx {
 
 /* ------------------------------------------------------------------ the interpreter */
 
-/* handler-case generators: one case per eBPF register */
-#define RC10(FAM, M, A, B)                                                                  \
-    case (FAM)*GX_HSTRIDE + 0: { M(r0, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 1: { M(r1, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 2: { M(r2, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 3: { M(r3, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 4: { M(r4, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 5: { M(r5, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 6: { M(r6, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 7: { M(r7, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 8: { M(r8, A, B) } break;                                               \
-    case (FAM)*GX_HSTRIDE + 9: { M(r9, A, B) } break;
-#define RC11(FAM, M, A, B) RC10(FAM, M, A, B) case (FAM)*GX_HSTRIDE + 10: { M(r10, A, B) } break;
+/* case generators over the operation lists of gx_layout.h */
+#define ALU_CASE(P, NAME, O, W, OPND) \
+    case GXO_##P##NAME: R[d] = W<O>(R[d], OPND); break;
+#define ALU_FORM(P, W, OPND)                                                                     \
+    ALU_CASE(P, ADD, O_ADD, W, OPND) ALU_CASE(P, SUB, O_SUB, W, OPND) ALU_CASE(P, MUL, O_MUL, W, OPND) \
+    ALU_CASE(P, DIV, O_DIV, W, OPND) ALU_CASE(P, SDIV, O_SDIV, W, OPND)                          \
+    ALU_CASE(P, MOD, O_MOD, W, OPND) ALU_CASE(P, SMOD, O_SMOD, W, OPND)                          \
+    ALU_CASE(P, OR, O_OR, W, OPND) ALU_CASE(P, AND, O_AND, W, OPND) ALU_CASE(P, XOR, O_XOR, W, OPND) \
+    ALU_CASE(P, LSH, O_LSH, W, OPND) ALU_CASE(P, RSH, O_RSH, W, OPND) ALU_CASE(P, ARSH, O_ARSH, W, OPND) \
+    ALU_CASE(P, MOV, O_MOV, W, OPND)
 
-#define IMM ((int32_t)(u >> 32))
-#define AUX ((u32)(u >> 16) & 0xFFFFu)
-#define SGL(k) (GX_SINGLE_BASE + (k))
+/* a conditional jump: the taken lanes go to aux; a split of the warp switches to min-pc mode */
+#define JMP_CASE(P, NAME, C, W, OPND) \
+    case GXO_##P##NAME: taken = W<C>(R[d], OPND); goto jump;
+#define JMP_FORM(P, W, OPND)                                                                     \
+    JMP_CASE(P, JEQ, C_EQ, W, OPND) JMP_CASE(P, JNE, C_NE, W, OPND) JMP_CASE(P, JGT, C_GT, W, OPND) \
+    JMP_CASE(P, JGE, C_GE, W, OPND) JMP_CASE(P, JLT, C_LT, W, OPND) JMP_CASE(P, JLE, C_LE, W, OPND) \
+    JMP_CASE(P, JSGT, C_SGT, W, OPND) JMP_CASE(P, JSGE, C_SGE, W, OPND)                          \
+    JMP_CASE(P, JSLT, C_SLT, W, OPND) JMP_CASE(P, JSLE, C_SLE, W, OPND) JMP_CASE(P, JSET, C_SET, W, OPND)
 
-#define H_A64K(R, O, _) R = a64<O>(R, sx32(IMM)); pc++;
-#define H_A64T(R, O, _) R = a64<O>(R, T); pc++;
-#define H_A32K(R, O, _) R = a32<O>(R, (u64)(u32)IMM); pc++;
-#define H_A32T(R, O, _) R = a32<O>(R, T); pc++;
-#define ALU_GROUP(OPNAME, O)                        \
-    RC10(GXF_##OPNAME##64K, H_A64K, O, 0)           \
-    RC10(GXF_##OPNAME##64T, H_A64T, O, 0)           \
-    RC10(GXF_##OPNAME##32K, H_A32K, O, 0)           \
-    RC10(GXF_##OPNAME##32T, H_A32T, O, 0)
+#define LD_FORM(P, ADDR)                                                                         \
+    case GXO_##P##1: R[d] = load_sz<1, false>(ADDR); break;                                      \
+    case GXO_##P##2: R[d] = load_sz<2, false>(ADDR); break;                                      \
+    case GXO_##P##4: R[d] = load_sz<4, false>(ADDR); break;                                      \
+    case GXO_##P##8: R[d] = load_sz<8, false>(ADDR); break;                                      \
+    case GXO_##P##S1: R[d] = load_sz<1, true>(ADDR); break;                                      \
+    case GXO_##P##S2: R[d] = load_sz<2, true>(ADDR); break;                                      \
+    case GXO_##P##S4: R[d] = load_sz<4, true>(ADDR); break;
 
-/* accumulator forms of the rare ALU operations */
-#define SLOW_GROUP(OPNAME, O)                                                                 \
-    case SGL(GXS_##OPNAME##64K): A = a64<O>(A, sx32(IMM)); pc++; break;                       \
-    case SGL(GXS_##OPNAME##64T): A = a64<O>(A, T); pc++; break;                               \
-    case SGL(GXS_##OPNAME##32K): A = a32<O>(A, (u64)(u32)IMM); pc++; break;                   \
-    case SGL(GXS_##OPNAME##32T): A = a32<O>(A, T); pc++; break;
+#define ST_FORM(P, ADDR, VAL)                                                                    \
+    case GXO_##P##1: store_sz<1>(ADDR, VAL); break;                                              \
+    case GXO_##P##2: store_sz<2>(ADDR, VAL); break;                                              \
+    case GXO_##P##4: store_sz<4>(ADDR, VAL); break;                                              \
+    case GXO_##P##8: store_sz<8>(ADDR, VAL); break;
 
-#define JUMP_TO(TK)                                                                          \
-    {                                                                                        \
-        const bool tk_ = (TK);                                                               \
-        const u32 np_ = tk_ ? AUX : pc + 1;                                                  \
-        if (!div) {                                                                          \
-            const u32 b_ = __ballot_sync(FULLM, tk_);                                        \
-            if (b_ != 0 && b_ != FULLM) div = true;                                          \
-        }                                                                                    \
-        if (np_ <= pc && ++back > env.budget) goto budget_trip;                              \
-        pc = np_;                                                                            \
-    }
-
-#define H_J64K(R, C, _) JUMP_TO(c64<C>(R, sx32(IMM)))
-#define H_J64T(R, C, _) JUMP_TO(c64<C>(R, T))
-#define H_J32K(R, C, _) JUMP_TO(c32<C>(R, (u64)(u32)IMM))
-#define JMP_GROUP(OPNAME, C)                        \
-    RC10(GXF_##OPNAME##64K, H_J64K, C, 0)           \
-    RC10(GXF_##OPNAME##64T, H_J64T, C, 0)           \
-    RC10(GXF_##OPNAME##32K, H_J32K, C, 0)           \
-    case SGL(GXS_##OPNAME##32A): JUMP_TO(c32<C>(A, T)) break;
-
-/* ctx word w of this lane lives at ctxw[w * env.ctx_row + lane]; AUX is the byte offset */
-#define CTX_PTR ((const uint8_t *)(ctxw + (AUX >> 3) * env.ctx_row + lane) + (AUX & 7))
-#define H_LDC(R, SZ, SG) R = load_sz<SZ, SG>(CTX_PTR); pc++;
-#define H_LDS(R, SZ, SG) R = load_sz<SZ, SG>((const uint8_t *)stack + AUX); pc++;
-#define H_LDM(R, SZ, SG) R = load_sz<SZ, SG>((const uint8_t *)B + IMM); pc++;
-#define H_STS(R, SZ, _) store_sz<SZ>((uint8_t *)stack + AUX, R); pc++;
-#define H_MOVT(R, _a, _b) T = R; pc++;
-#define H_MOVA(R, _a, _b) A = R; pc++;
-#define H_MOVB(R, _a, _b) B = R; pc++;
-#define H_MOVR(R, _a, _b) R = T; pc++;
-#define H_MOVRA(R, _a, _b) R = A; pc++;
-#define H_LDIMM(R, _a, _b) R = (u64)(u32)IMM | ((u64)(u32)(env.uops[pc + 1] >> 32) << 32); pc += 2;
-
-#define ST_IMM(SZ, ADDR) store_sz<SZ>((uint8_t *)(ADDR), sx32(IMM)); pc++; break;
-#define ATOM(OP, SZ) agg_update<OP, SZ>(B + (u64)(s64)IMM, T, exec); pc++; break;
-#define ATOMF(OP, SZ) T = fetch_update<OP, SZ>(B + (u64)(s64)IMM, T); pc++; break;
+/* atomics at ADDR with the value in R[s]: plain (warp-aggregated), fetching, xchg, cmpxchg */
+#define ATOM_FORM(P, ADDR)                                                                       \
+    case GXO_##P##ADD4: agg_update<AG_ADD, 4>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##OR4: agg_update<AG_OR, 4>(ADDR, R[s], exec); break;                            \
+    case GXO_##P##AND4: agg_update<AG_AND, 4>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##XOR4: agg_update<AG_XOR, 4>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##ADD8: agg_update<AG_ADD, 8>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##OR8: agg_update<AG_OR, 8>(ADDR, R[s], exec); break;                            \
+    case GXO_##P##AND8: agg_update<AG_AND, 8>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##XOR8: agg_update<AG_XOR, 8>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##FADD4: R[s] = fetch_update<AG_ADD, 4>(ADDR, R[s]); break;                      \
+    case GXO_##P##FOR4: R[s] = fetch_update<AG_OR, 4>(ADDR, R[s]); break;                        \
+    case GXO_##P##FAND4: R[s] = fetch_update<AG_AND, 4>(ADDR, R[s]); break;                      \
+    case GXO_##P##FXOR4: R[s] = fetch_update<AG_XOR, 4>(ADDR, R[s]); break;                      \
+    case GXO_##P##FADD8: R[s] = fetch_update<AG_ADD, 8>(ADDR, R[s]); break;                      \
+    case GXO_##P##FOR8: R[s] = fetch_update<AG_OR, 8>(ADDR, R[s]); break;                        \
+    case GXO_##P##FAND8: R[s] = fetch_update<AG_AND, 8>(ADDR, R[s]); break;                      \
+    case GXO_##P##FXOR8: R[s] = fetch_update<AG_XOR, 8>(ADDR, R[s]); break;                      \
+    case GXO_##P##XCHG4: R[s] = xchg<4>(ADDR, R[s]); break;                                      \
+    case GXO_##P##XCHG8: R[s] = xchg<8>(ADDR, R[s]); break;                                      \
+    case GXO_##P##CMPX4: R[0] = cmpxchg<4>(ADDR, R[0], R[s]); break;                             \
+    case GXO_##P##CMPX8: R[0] = cmpxchg<8>(ADDR, R[0], R[s]); break;
 
 /*
  * Interpret one event per lane.  All 32 lanes of the warp call this together; lanes
  * without an event pass valid = false.  Returns R0.
+ *
+ * Each micro-op is one 16-byte shared-memory load (the same address for every lane at the
+ * same pc) and one dispatch over the dense operation ids; R0..R10 sit in a per-thread
+ * array indexed by the micro-op's register fields (local memory, served by L1).  While all
+ * lanes sit at the same pc the warp runs in uniform mode; after a split branch it runs
+ * "min-pc" mode (only lanes at the smallest pc advance), which re-converges
+ * forward-branching code at its join points.
  */
 __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool valid, u64 ev_idx) {
     const u32 lane = lane_id();
     u64 stack[GX_STACK_BYTES / 8];
-    u64 r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0;
-    u64 r10 = (u64)(stack + GX_STACK_BYTES / 8);
-    u64 T = 0, A = 0, B = 0;
+    u64 R[11];
+#pragma unroll
+    for (int k = 0; k < 10; k++) R[k] = 0;
+    R[10] = (u64)(stack + GX_STACK_BYTES / 8);
+    const ulonglong2 *uops = (const ulonglong2 *)env.uops;
     u32 pc = valid ? 0u : PC_DONE;
     u32 exec = __ballot_sync(FULLM, valid);
     bool div = exec != FULLM;
@@ -131,172 +126,102 @@ __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool vali
             if (exec == FULLM) div = false;
             if (pc != mpc) continue;
         }
-        const u64 u = env.uops[pc];
-        switch ((u32)u & 0xFFFFu) {
-            RC11(GXF_MOVT, H_MOVT, 0, 0)
-            RC11(GXF_MOVA, H_MOVA, 0, 0)
-            RC11(GXF_MOVB, H_MOVB, 0, 0)
-            RC10(GXF_MOVR, H_MOVR, 0, 0)
-            RC10(GXF_MOVRA, H_MOVRA, 0, 0)
-            RC10(GXF_LDIMM64, H_LDIMM, 0, 0)
-            ALU_GROUP(ADD, O_ADD)
-            ALU_GROUP(SUB, O_SUB)
-            ALU_GROUP(MUL, O_MUL)
-            ALU_GROUP(OR, O_OR)
-            ALU_GROUP(AND, O_AND)
-            ALU_GROUP(XOR, O_XOR)
-            ALU_GROUP(LSH, O_LSH)
-            ALU_GROUP(RSH, O_RSH)
-            ALU_GROUP(MOV, O_MOV)
-            JMP_GROUP(JEQ, C_EQ)
-            JMP_GROUP(JNE, C_NE)
-            JMP_GROUP(JGT, C_GT)
-            JMP_GROUP(JGE, C_GE)
-            JMP_GROUP(JLT, C_LT)
-            JMP_GROUP(JLE, C_LE)
-            JMP_GROUP(JSGT, C_SGT)
-            JMP_GROUP(JSGE, C_SGE)
-            JMP_GROUP(JSLT, C_SLT)
-            JMP_GROUP(JSLE, C_SLE)
-            JMP_GROUP(JSET, C_SET)
-            RC10(GXF_LDXC1, H_LDC, 1, false)
-            RC10(GXF_LDXC2, H_LDC, 2, false)
-            RC10(GXF_LDXC4, H_LDC, 4, false)
-            RC10(GXF_LDXC8, H_LDC, 8, false)
-            RC10(GXF_LDXCS1, H_LDC, 1, true)
-            RC10(GXF_LDXCS2, H_LDC, 2, true)
-            RC10(GXF_LDXCS4, H_LDC, 4, true)
-            RC10(GXF_LDXS1, H_LDS, 1, false)
-            RC10(GXF_LDXS2, H_LDS, 2, false)
-            RC10(GXF_LDXS4, H_LDS, 4, false)
-            RC10(GXF_LDXS8, H_LDS, 8, false)
-            RC10(GXF_LDXSS1, H_LDS, 1, true)
-            RC10(GXF_LDXSS2, H_LDS, 2, true)
-            RC10(GXF_LDXSS4, H_LDS, 4, true)
-            RC10(GXF_LDXM1, H_LDM, 1, false)
-            RC10(GXF_LDXM2, H_LDM, 2, false)
-            RC10(GXF_LDXM4, H_LDM, 4, false)
-            RC10(GXF_LDXM8, H_LDM, 8, false)
-            RC10(GXF_LDXMS1, H_LDM, 1, true)
-            RC10(GXF_LDXMS2, H_LDM, 2, true)
-            RC10(GXF_LDXMS4, H_LDM, 4, true)
-            RC10(GXF_STXS1, H_STS, 1, 0)
-            RC10(GXF_STXS2, H_STS, 2, 0)
-            RC10(GXF_STXS4, H_STS, 4, 0)
-            RC10(GXF_STXS8, H_STS, 8, 0)
-
-            SLOW_GROUP(DIV, O_DIV)
-            SLOW_GROUP(SDIV, O_SDIV)
-            SLOW_GROUP(MOD, O_MOD)
-            SLOW_GROUP(SMOD, O_SMOD)
-            SLOW_GROUP(ARSH, O_ARSH)
-        case SGL(GXS_NEG64): A = (u64)0 - A; pc++; break;
-        case SGL(GXS_NEG32): A = (u64)(u32)(0u - (u32)A); pc++; break;
-        case SGL(GXS_MOVSX64_8): A = (u64)(s64)(int8_t)T; pc++; break;
-        case SGL(GXS_MOVSX64_16): A = (u64)(s64)(int16_t)T; pc++; break;
-        case SGL(GXS_MOVSX64_32): A = (u64)(s64)(int32_t)T; pc++; break;
-        case SGL(GXS_MOVSX32_8): A = (u64)(u32)(int32_t)(int8_t)T; pc++; break;
-        case SGL(GXS_MOVSX32_16): A = (u64)(u32)(int32_t)(int16_t)T; pc++; break;
-        case SGL(GXS_LE16): A &= 0xFFFFull; pc++; break;
-        case SGL(GXS_LE32): A &= 0xFFFFFFFFull; pc++; break;
-        case SGL(GXS_BSWAP16): A = (u64)__byte_perm((u32)A, 0u, 0x4401u); pc++; break;
-        case SGL(GXS_BSWAP32): A = (u64)__byte_perm((u32)A, 0u, 0x0123u); pc++; break;
-        case SGL(GXS_BSWAP64):
-            A = ((u64)__byte_perm((u32)A, 0u, 0x0123u) << 32) | (u64)__byte_perm((u32)(A >> 32), 0u, 0x0123u);
-            pc++;
+        const ulonglong2 u = uops[pc];
+        const u32 w = (u32)u.x;
+        const u32 d = (w >> 8) & 0xFu, s = (w >> 12) & 0xFu, aux = w >> 16;
+        const int32_t imm = (int32_t)(u.x >> 32);
+        bool taken;
+        switch (w & 0xFFu) {
+            ALU_FORM(A64K_, a64, (u64)(s64)imm)
+            ALU_FORM(A64X_, a64, R[s])
+            ALU_FORM(A32K_, a32, (u64)(u32)imm)
+            ALU_FORM(A32X_, a32, R[s])
+        case GXO_NEG64: R[d] = (u64)0 - R[d]; break;
+        case GXO_NEG32: R[d] = (u64)(u32)(0u - (u32)R[d]); break;
+        case GXO_MOVSX64_8: R[d] = (u64)(s64)(int8_t)R[s]; break;
+        case GXO_MOVSX64_16: R[d] = (u64)(s64)(int16_t)R[s]; break;
+        case GXO_MOVSX64_32: R[d] = (u64)(s64)(int32_t)R[s]; break;
+        case GXO_MOVSX32_8: R[d] = (u64)(u32)(int32_t)(int8_t)R[s]; break;
+        case GXO_MOVSX32_16: R[d] = (u64)(u32)(int32_t)(int16_t)R[s]; break;
+        case GXO_LE16: R[d] &= 0xFFFFull; break;
+        case GXO_LE32: R[d] &= 0xFFFFFFFFull; break;
+        case GXO_BSWAP16: R[d] = (u64)__byte_perm((u32)R[d], 0u, 0x4401u); break;
+        case GXO_BSWAP32: R[d] = (u64)__byte_perm((u32)R[d], 0u, 0x0123u); break;
+        case GXO_BSWAP64: {
+            const u64 x = R[d];
+            R[d] = ((u64)__byte_perm((u32)x, 0u, 0x0123u) << 32) | (u64)__byte_perm((u32)(x >> 32), 0u, 0x0123u);
             break;
-        case SGL(GXS_ST_S1): ST_IMM(1, (uint8_t *)stack + AUX)
-        case SGL(GXS_ST_S2): ST_IMM(2, (uint8_t *)stack + AUX)
-        case SGL(GXS_ST_S4): ST_IMM(4, (uint8_t *)stack + AUX)
-        case SGL(GXS_ST_S8): ST_IMM(8, (uint8_t *)stack + AUX)
-        case SGL(GXS_ST_M1): ST_IMM(1, B + (s64)(int16_t)AUX)
-        case SGL(GXS_ST_M2): ST_IMM(2, B + (s64)(int16_t)AUX)
-        case SGL(GXS_ST_M4): ST_IMM(4, B + (s64)(int16_t)AUX)
-        case SGL(GXS_ST_M8): ST_IMM(8, B + (s64)(int16_t)AUX)
-        case SGL(GXS_STT_S1): store_sz<1>((uint8_t *)stack + AUX, T); pc++; break;
-        case SGL(GXS_STT_S2): store_sz<2>((uint8_t *)stack + AUX, T); pc++; break;
-        case SGL(GXS_STT_S4): store_sz<4>((uint8_t *)stack + AUX, T); pc++; break;
-        case SGL(GXS_STT_S8): store_sz<8>((uint8_t *)stack + AUX, T); pc++; break;
-        case SGL(GXS_STT_M1): store_sz<1>((uint8_t *)(B + (u64)(s64)IMM), T); pc++; break;
-        case SGL(GXS_STT_M2): store_sz<2>((uint8_t *)(B + (u64)(s64)IMM), T); pc++; break;
-        case SGL(GXS_STT_M4): store_sz<4>((uint8_t *)(B + (u64)(s64)IMM), T); pc++; break;
-        case SGL(GXS_STT_M8): store_sz<8>((uint8_t *)(B + (u64)(s64)IMM), T); pc++; break;
-        case SGL(GXS_AADD4): ATOM(AG_ADD, 4)
-        case SGL(GXS_AOR4): ATOM(AG_OR, 4)
-        case SGL(GXS_AAND4): ATOM(AG_AND, 4)
-        case SGL(GXS_AXOR4): ATOM(AG_XOR, 4)
-        case SGL(GXS_AADD8): ATOM(AG_ADD, 8)
-        case SGL(GXS_AOR8): ATOM(AG_OR, 8)
-        case SGL(GXS_AAND8): ATOM(AG_AND, 8)
-        case SGL(GXS_AXOR8): ATOM(AG_XOR, 8)
-        case SGL(GXS_AFADD4): ATOMF(AG_ADD, 4)
-        case SGL(GXS_AFOR4): ATOMF(AG_OR, 4)
-        case SGL(GXS_AFAND4): ATOMF(AG_AND, 4)
-        case SGL(GXS_AFXOR4): ATOMF(AG_XOR, 4)
-        case SGL(GXS_AFADD8): ATOMF(AG_ADD, 8)
-        case SGL(GXS_AFOR8): ATOMF(AG_OR, 8)
-        case SGL(GXS_AFAND8): ATOMF(AG_AND, 8)
-        case SGL(GXS_AFXOR8): ATOMF(AG_XOR, 8)
-        case SGL(GXS_AXCHG4): T = xchg<4>(B + (u64)(s64)IMM, T); pc++; break;
-        case SGL(GXS_AXCHG8): T = xchg<8>(B + (u64)(s64)IMM, T); pc++; break;
-        case SGL(GXS_ACMPX4): r0 = cmpxchg<4>(B + (u64)(s64)IMM, r0, T); pc++; break;
-        case SGL(GXS_ACMPX8): r0 = cmpxchg<8>(B + (u64)(s64)IMM, r0, T); pc++; break;
-        case SGL(GXS_JA): JUMP_TO(true) break;
-        case SGL(GXS_NOP): pc++; break;
-        case SGL(GXS_MOVB_STK): B = (u64)((uint8_t *)stack + AUX); pc++; break;
-        case SGL(GXS_EXIT):
+        }
+        case GXO_LDIMM64: R[d] = u.y; break;
+            JMP_FORM(J64K_, c64, (u64)(s64)imm)
+            JMP_FORM(J64X_, c64, R[s])
+            JMP_FORM(J32K_, c32, (u64)(u32)imm)
+            JMP_FORM(J32X_, c32, R[s])
+        case GXO_JA: taken = true; goto jump;
+        case GXO_EXIT:
             if (!div) goto finished;
             pc = PC_DONE;
+            continue;
+        case GXO_NOP: break;
+            /* ctx word k of this lane lives at ctxw[k * env.ctx_row + lane]; aux is the byte offset */
+            LD_FORM(LDC, (const uint8_t *)(ctxw + (aux >> 3) * env.ctx_row + lane) + (aux & 7))
+            LD_FORM(LDS, (const uint8_t *)stack + aux)
+            LD_FORM(LDM, (const uint8_t *)(R[s] + (u64)(s64)imm))
+            ST_FORM(STIS, (uint8_t *)stack + aux, (u64)(s64)imm)
+            ST_FORM(STIM, (uint8_t *)(R[d] + (u64)(s64)(int16_t)aux), (u64)(s64)imm)
+            ST_FORM(STXS, (uint8_t *)stack + aux, R[s])
+            ST_FORM(STXM, (uint8_t *)(R[d] + (u64)(s64)imm), R[s])
+            ATOM_FORM(AS_, (u64)((uint8_t *)stack + aux))
+            ATOM_FORM(AM_, R[d] + (u64)(s64)imm)
+        case GXO_CALL_LOOKUP: R[0] = map_lookup(env.maps[R[1]], (const uint8_t *)R[2], exec, env.stats); break;
+        case GXO_CALL_UPDATE:
+            R[0] = (u64)(s64)map_update(env.maps[R[1]], (const uint8_t *)R[2], (const uint8_t *)R[3], R[4], exec,
+                                        env.stats);
             break;
-        case SGL(GXS_CALL_LOOKUP):
-            r0 = map_lookup(env.maps[r1], (const uint8_t *)r2, exec, env.stats);
-            pc++;
-            break;
-        case SGL(GXS_CALL_UPDATE):
-            r0 = (u64)(s64)map_update(env.maps[r1], (const uint8_t *)r2, (const uint8_t *)r3, r4, exec, env.stats);
-            pc++;
-            break;
-        case SGL(GXS_CALL_DELETE): {
-            const gx_dmap &m = env.maps[r1];
-            r0 = (u64)(s64)(m.type == GX_MAP_HASH ? hash_delete(m, (const uint8_t *)r2, env.stats) : GX_EINVAL);
-            pc++;
-            break;
-        }
-        case SGL(GXS_CALL_RB_RESERVE):
-            r0 = rb_reserve(env.maps[r1], r2, exec, ev_idx);
-            pc++;
-            break;
-        case SGL(GXS_CALL_RB_OUTPUT): {
-            const u64 p = rb_reserve(env.maps[r1], r3, exec, ev_idx);
-            if (p) copy_bytes((uint8_t *)p, (const uint8_t *)r2, (u32)r3);
-            r0 = p ? 0 : (u64)(s64)GX_EAGAIN;
-            pc++;
+        case GXO_CALL_DELETE: {
+            const gx_dmap &m = env.maps[R[1]];
+            R[0] = (u64)(s64)(m.type == GX_MAP_HASH ? hash_delete(m, (const uint8_t *)R[2], env.stats) : GX_EINVAL);
             break;
         }
-        case SGL(GXS_CALL_RB_SUBMIT): pc++; break; /* records are committed when reserved */
-        case SGL(GXS_CALL_RB_DISCARD):
-            ((u32 *)(r1 - GX_RB_HDR))[1] = GX_RB_DISCARDED;
-            pc++;
+        case GXO_CALL_RB_RESERVE: R[0] = rb_reserve(env.maps[R[1]], R[2], exec, ev_idx); break;
+        case GXO_CALL_RB_OUTPUT: {
+            const u64 p = rb_reserve(env.maps[R[1]], R[3], exec, ev_idx);
+            if (p) copy_bytes((uint8_t *)p, (const uint8_t *)R[2], (u32)R[3]);
+            R[0] = p ? 0 : (u64)(s64)GX_EAGAIN;
             break;
-        case SGL(GXS_CALL_AMAX): agg_update<AG_MAX, 8>(r1, r2, exec); pc++; break;
-        case SGL(GXS_CALL_AMIN): agg_update<AG_MIN, 8>(r1, r2, exec); pc++; break;
+        }
+        case GXO_CALL_RB_SUBMIT: break; /* records are committed when reserved */
+        case GXO_CALL_RB_DISCARD: ((u32 *)(R[1] - GX_RB_HDR))[1] = GX_RB_DISCARDED; break;
+        case GXO_CALL_AMAX: agg_update<AG_MAX, 8>(R[1], R[2], exec); break;
+        case GXO_CALL_AMIN: agg_update<AG_MIN, 8>(R[1], R[2], exec); break;
         default:
             set_status(env.stats, GX_E_DEVICE);
-            r0 = 0;
+            R[0] = 0;
             pc = PC_DONE;
             if (!div) goto finished;
-            break;
+            continue;
         }
+        pc++;
         continue;
+    jump: {
+        const u32 np = taken ? aux : pc + 1;
+        if (!div) {
+            const u32 b = __ballot_sync(FULLM, taken);
+            if (b != 0 && b != FULLM) div = true;
+        }
+        if (np <= pc && ++back > env.budget) goto budget_trip;
+        pc = np;
+        continue;
+    }
     budget_trip:
         atomicAdd(&env.stats[GX_STAT_BUDGET], 1ull);
         set_status(env.stats, GX_E_BUDGET);
-        r0 = 0;
+        R[0] = 0;
         pc = PC_DONE;
         if (!div) break;
     }
 finished:
-    return r0;
+    return R[0];
 }
 
 /* ------------------------------------------------------------------ kernels */
