@@ -65,6 +65,7 @@ extern "C" {
 #define GX_E_DEVICE (-1004)    /* device-side invariant violated (sticky status) */
 #define GX_E_ADMISSION (-1005) /* request larger than the server's memory budget */
 #define GX_E_NODEV (-1006)     /* no CUDA device or wrong architecture */
+#define GX_E_FAULT (-1007)     /* checked program: an access outside its regions was stopped */
 
 /* ---------------------------------------------------------------- map types (Linux enum values) */
 #define GX_MAP_HASH 1
@@ -255,6 +256,20 @@ typedef struct gx_prog_opts {
  * returns GX_E_NODEV if the runtime compiler is unavailable.
  */
 #define GX_PROG_JIT 1u
+/*
+ * opts.flags: GX_PROG_CHECKED runs the program through a checked build of the
+ * interpreter, which tests every memory access against the regions the event may touch
+ * before making it: the record it reads (ctx, read-only), its 512-byte stack, the value
+ * memory of the program's maps and the data of its ring buffers, with natural alignment;
+ * and every helper's map index and buffer arguments.  An access that fails is not made:
+ * the event stops with R0 = 0, the status becomes GX_E_FAULT and gx_run_stats.fault_pc
+ * names the first failing micro-op.  It is the device-side stand-in for a memory checker,
+ * for a program the verifier accepted: with a sound verifier nothing fails, and results
+ * equal the unchecked tiers'.  The checked build runs every step in its divergent form,
+ * so it is several times slower.  Not with GX_PROG_JIT (GX_EINVAL); plain launches only
+ * (batches and servers refuse a checked program with GX_EINVAL).
+ */
+#define GX_PROG_CHECKED 2u
 
 /*
  * Host only: verify a program and compile its specialised form to sm_103a code without
@@ -472,8 +487,9 @@ int gx_run_batch_ex(gx_prog *prog, const void *events_dev, uint64_t n, uint64_t 
 int gx_run_batch_host(gx_prog *prog, const void *events_host, uint64_t n, int64_t *ret_out_host);
 
 typedef struct gx_run_stats {
-    int32_t status;         /* first device error (GX_E_BUDGET, GX_E_TIMEOUT, GX_E_DEVICE) or 0 */
-    uint32_t reserved;
+    int32_t status;         /* first device error (GX_E_BUDGET, GX_E_TIMEOUT, GX_E_DEVICE, GX_E_FAULT) or 0 */
+    uint32_t fault_pc;      /* GX_PROG_CHECKED: 1 + the micro-op (instruction) index of the first stopped
+                               access, 0 if none */
     uint64_t budget_trips;  /* events stopped by the instruction budget */
     uint64_t waits_expired; /* bounded device waits that gave up */
     uint64_t launches;      /* kernel launches issued for this program */

@@ -4,7 +4,7 @@ The native library (verifier, decoder, CUDA kernels, runtime) is built in-tree b
 `_build.build()` and bound by `gx.py`; see include/gx.h for the C ABI.
 """
 from .gx import (  # noqa: F401
-    ANY, E_ADMISSION, E_BUDGET, E_CUDA, E_DEVICE, E_NODEV, E_TIMEOUT, E_VERIFY, E2BIG, EAGAIN, EEXIST, EINVAL,
+    ANY, E_ADMISSION, E_BUDGET, E_CUDA, E_DEVICE, E_FAULT, E_NODEV, PROG_CHECKED, E_TIMEOUT, E_VERIFY, E2BIG, EAGAIN, EEXIST, EINVAL,
     ENOENT, ENOMEM, EXIST, MAP_ARRAY, MAP_F_NO_DELETE, MAP_HASH, MAP_RINGBUF, NOEXIST, SHARDS_AGG, SHARDS_OFF, Batch, Context, GxError, Map, Program,
     GRID_PER_CHUNK, Server, VARIANT_CAPPED, VARIANT_WIDE, analyze, check, exported_symbols, jit_check, lib, now, parse_records, precompile, verify,
     SIMT_V_ATOMIC, SIMT_V_BRANCH, SIMT_V_HELPER, SIMT_V_HELPERS, SIMT_V_INSNS, SIMT_V_KEY, SIMT_V_MEM, SIMT_V_NONE,

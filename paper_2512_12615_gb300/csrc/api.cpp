@@ -141,7 +141,8 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
     if (lp.grid != GX_GRID_PER_CHUNK) {
         uint64_t cap = lp.grid;
         if (cap == 0) { /* one wave: the blocks the device holds at once loop over the chunks */
-            const uint64_t key = ((uint64_t)block << 40) | (smem << 3) | lp.variant;
+            const bool checked = (p->opts.flags & GX_PROG_CHECKED) != 0;
+            const uint64_t key = ((uint64_t)block << 40) | (smem << 4) | (checked ? 8u : 0u) | lp.variant;
             int occ = 0;
             bool known = false;
             {
@@ -156,7 +157,7 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
                 if (p->jit) rc = cuda_status(jit_set_smem(p->jk, smem));
                 cudaError_t e = rc ? cudaSuccess
                                    : p->jit ? jit_occupancy(p->jk, (int)block, smem, &occ, lp.variant)
-                                            : exec_occupancy((int)block, smem, &occ);
+                                            : exec_occupancy((int)block, smem, &occ, checked);
                 if (rc == GX_OK && e != cudaSuccess) {
                     cudaGetLastError();
                     rc = GX_E_CUDA;
@@ -189,7 +190,7 @@ int launch_plain(gx_prog *p, const uint8_t *image, uint32_t image_bytes, const v
         if (rc == GX_OK)
             rc = cuda_status(jit_launch(p->jk, P, (unsigned)grid, block, smem, s, lp.variant));
     } else {
-        rc = cuda_status(launch_exec(P, (unsigned)grid, block, smem, s));
+        rc = cuda_status(launch_exec(P, (unsigned)grid, block, smem, s, (p->opts.flags & GX_PROG_CHECKED) != 0));
     }
     if (rc == GX_OK) p->launches++;
     return rc;
@@ -516,6 +517,7 @@ int gx_merge_ops(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uin
                  const gx_prog_opts *opts, uint32_t map_index, uint8_t *word_ops, uint8_t *insert_value,
                  uint32_t *has_insert, char *log, size_t log_len) {
     if (!insns || !opts || !word_ops || (n_maps && !maps) || map_index >= n_maps) return GX_EINVAL;
+    static_assert(GX_MAP_HASH_T == GX_MAP_HASH && GX_MAP_RINGBUF_T == GX_MAP_RINGBUF, "map types of gx_layout.h");
     static_assert(UC_ADD == GX_MERGE_ADD && UC_OR == GX_MERGE_OR && UC_AND == GX_MERGE_AND && UC_XOR == GX_MERGE_XOR &&
                       UC_MAX == GX_MERGE_MAX && UC_MIN == GX_MERGE_MIN && UC_W8 == GX_MERGE_W8,
                   "the ABI's merge codes are the verifier's update classes");
@@ -588,7 +590,8 @@ int gx_verify_simt(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, u
 int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *maps, uint32_t n_maps,
                    const gx_prog_opts *opts, gx_prog **out, char *log, size_t log_len) {
     if (!c || !insns || !opts || !out || (n_maps && !maps)) return GX_EINVAL;
-    if (opts->flags & ~GX_PROG_JIT) return GX_EINVAL;
+    if (opts->flags & ~(GX_PROG_JIT | GX_PROG_CHECKED)) return GX_EINVAL;
+    if ((opts->flags & GX_PROG_JIT) && (opts->flags & GX_PROG_CHECKED)) return GX_EINVAL; /* checks: interpreter only */
     *out = nullptr;
     std::vector<gx_map_spec> specs(n_maps);
     for (uint32_t i = 0; i < n_maps; i++) {
@@ -844,6 +847,7 @@ int gx_last_status(gx_prog *p, gx_run_stats *out, int reset, void *stream) {
     if (cudaMemcpy(st, p->dstats, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return GX_E_CUDA;
     memset(out, 0, sizeof *out);
     out->status = (int32_t)(uint32_t)st[GX_STAT_STATUS];
+    out->fault_pc = (uint32_t)st[GX_STAT_FAULT];
     if (out->status == GX_E_TIMEOUT && p->sched_lc) p->ctx->launch_control_timed_out = true;
     out->budget_trips = st[GX_STAT_BUDGET];
     out->waits_expired = st[GX_STAT_WAITS];

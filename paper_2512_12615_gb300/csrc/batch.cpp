@@ -314,7 +314,7 @@ int gx_batch_create(gx_ctx *c, gx_batch **out) {
 
 int gx_batch_add(gx_batch *b, gx_prog *p, const void *events, uint64_t n, int64_t *ret_out) {
     if (!b || !p || p->ctx != b->ctx || (!events && n) || (((uintptr_t)events) & 15)) return GX_EINVAL;
-    if (b->planned) return GX_EINVAL;
+    if (b->planned || (p->opts.flags & GX_PROG_CHECKED)) return GX_EINVAL; /* checked programs: plain launches */
     b->items.push_back(Item{p, events, n, ret_out});
     return GX_OK;
 }
@@ -566,6 +566,7 @@ int gx_server_submit(gx_server *s, gx_prog *p, const void *events, uint64_t n, i
                      double t_arrival) {
     if (!s || !p || p->ctx != s->ctx || (!events && n) || (((uintptr_t)events) & 15)) return GX_EINVAL;
     if (s->jit && !s->prog_slot.count(p)) return GX_EINVAL; /* not part of the server's kernel */
+    if (p->opts.flags & GX_PROG_CHECKED) return GX_EINVAL;   /* checked programs: plain launches */
     gx_server::Req r{p, events, n, ret_out, tag, t_arrival > 0 ? t_arrival : now_s(), n * p->opts.ctx_size};
     std::lock_guard<std::mutex> g(s->mu);
     for (auto *m : p->maps)

@@ -631,6 +631,8 @@ struct ExecEnv {
     u32 wc_agg;    /* updates that miss the cache are warp-aggregated */
     u32 ctx_row;   /* words between rows of the event tile (GX_CTX_ROW) */
     uint8_t *shard; /* the block's combining area (shared memory) */
+    u32 n_maps;    /* the program's maps (descriptors at `maps`) */
+    u32 ctx_size;  /* bytes of one event record */
 };
 
 /* ------------------------------------------------------------------ block-private combining */
@@ -782,6 +784,8 @@ __device__ __forceinline__ ExecEnv stage_env_at(uint8_t *smem, u32 shard_off, u3
     env.wc_bits = wcp & 0xFFu;
     env.wc_agg = (wcp >> 8) & 1u;
     env.ctx_row = GX_CTX_ROW(hdr->ctx_size / 8);
+    env.n_maps = hdr->n_maps;
+    env.ctx_size = hdr->ctx_size;
     env.shard = smem + shard_off;
     return env;
 }

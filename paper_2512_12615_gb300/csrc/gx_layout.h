@@ -106,6 +106,7 @@ typedef struct gx_dprog_hdr {
 #define GX_STAT_STATUS 0
 #define GX_STAT_BUDGET 1
 #define GX_STAT_WAITS 2
+#define GX_STAT_FAULT 3 /* checked programs: 1 + the pc of the first stopped access */
 #define GX_STAT_WORDS 4
 
 /* persistent-kernel work item: events [begin, end) of one program */
@@ -141,6 +142,44 @@ typedef struct gx_exec_params {
                               updates that miss the cache are warp-aggregated */
     uint32_t shard_off;    /* byte offset of the combining area in dynamic shared memory */
 } gx_exec_params;
+
+/*
+ * Checked programs (GX_PROG_CHECKED): the regions an event may touch through a pointer.
+ * Written once for the device's checked interpreter and for host tests of the bounds.
+ */
+#if defined(__CUDACC__)
+#define GX_HD __host__ __device__ __forceinline__
+#else
+#define GX_HD static inline
+#endif
+#define GX_MAP_HASH_T 1u    /* GX_MAP_HASH of gx.h */
+#define GX_MAP_RINGBUF_T 27u /* GX_MAP_RINGBUF of gx.h */
+
+/* bytes of a map's value memory (a ring buffer: its data area) */
+GX_HD uint64_t gx_value_bytes(const gx_dmap *m) {
+    if (m->type == GX_MAP_RINGBUF_T) return m->mask;
+    if (m->type == GX_MAP_HASH_T) return (m->mask + 1) * (uint64_t)m->vstride;
+    return (uint64_t)m->max_entries * m->vstride;
+}
+
+/* [a, a + bytes) lies within the lane's stack or within one map's value memory (a ring
+   buffer's data): bytes >= 1, no wrap-around */
+GX_HD int gx_range_ok(const gx_dmap *maps, uint32_t n_maps, uint64_t stack_lo, uint32_t stack_bytes, uint64_t a,
+                      uint64_t bytes) {
+    if (bytes == 0 || a + bytes < a) return 0;
+    if (a >= stack_lo && a + bytes <= stack_lo + stack_bytes) return 1;
+    for (uint32_t i = 0; i < n_maps; i++) {
+        const uint64_t lo = (uint64_t)maps[i].values;
+        if (a >= lo && a + bytes <= lo + gx_value_bytes(&maps[i])) return 1;
+    }
+    return 0;
+}
+
+/* a load, store or atomic of `size` bytes (1, 2, 4, 8) at a: in range and naturally aligned */
+GX_HD int gx_access_ok(const gx_dmap *maps, uint32_t n_maps, uint64_t stack_lo, uint32_t stack_bytes, uint64_t a,
+                       uint32_t size) {
+    return (a & (uint64_t)(size - 1)) == 0 && gx_range_ok(maps, n_maps, stack_lo, stack_bytes, a, size);
+}
 
 #ifdef __cplusplus
 static_assert(sizeof(gx_dmap) == 64, "descriptor size");

@@ -57,43 +57,57 @@ namespace gx {
     JMP_CASE(P, JSGT, C_SGT, W, OPND) JMP_CASE(P, JSGE, C_SGE, W, OPND)                          \
     JMP_CASE(P, JSLT, C_SLT, W, OPND) JMP_CASE(P, JSLE, C_SLE, W, OPND) JMP_CASE(P, JSET, C_SET, W, OPND)
 
-#define LD_FORM(P, ADDR)                                                                         \
-    case GXO_##P##1: R[d] = load_sz<1, false>(ADDR); break;                                      \
-    case GXO_##P##2: R[d] = load_sz<2, false>(ADDR); break;                                      \
-    case GXO_##P##4: R[d] = load_sz<4, false>(ADDR); break;                                      \
-    case GXO_##P##8: R[d] = load_sz<8, false>(ADDR); break;                                      \
-    case GXO_##P##S1: R[d] = load_sz<1, true>(ADDR); break;                                      \
-    case GXO_##P##S2: R[d] = load_sz<2, true>(ADDR); break;                                      \
-    case GXO_##P##S4: R[d] = load_sz<4, true>(ADDR); break;
+/* checked programs: stop the event before an access that fails its check */
+#define CHK(OK)                     \
+    if (CHECKED && !(OK)) goto fault;
+#define CTX_OK(SZ) ((aux & ((SZ) - 1u)) == 0 && aux + (SZ) <= env.ctx_size)
+#define STK_OK(SZ) ((aux & ((SZ) - 1u)) == 0 && aux + (SZ) <= GX_STACK_BYTES)
+#define MEM_OK(A, SZ) gx_access_ok(env.maps, env.n_maps, (u64)stack, GX_STACK_BYTES, (u64)(A), (SZ))
+#define RANGE_OK(A, N) gx_range_ok(env.maps, env.n_maps, (u64)stack, GX_STACK_BYTES, (u64)(A), (N))
+#define LDM_OK(SZ) MEM_OK(R[s] + (u64)(s64)imm, SZ)
+#define STIM_OK(SZ) MEM_OK(R[d] + (u64)(s64)(int16_t)aux, SZ)
+#define DIMM_OK(SZ) MEM_OK(R[d] + (u64)(s64)imm, SZ)
+/* a helper's map argument: a map of the program, of the kind the helper takes */
+#define MAP_OK(IDX) ((IDX) < env.n_maps && env.maps[IDX].type != GX_MAP_RINGBUF)
+#define RING_OK(IDX) ((IDX) < env.n_maps && env.maps[IDX].type == GX_MAP_RINGBUF)
 
-#define ST_FORM(P, ADDR, VAL)                                                                    \
-    case GXO_##P##1: store_sz<1>(ADDR, VAL); break;                                              \
-    case GXO_##P##2: store_sz<2>(ADDR, VAL); break;                                              \
-    case GXO_##P##4: store_sz<4>(ADDR, VAL); break;                                              \
-    case GXO_##P##8: store_sz<8>(ADDR, VAL); break;
+#define LD_FORM(P, ADDR, OK)                                                                     \
+    case GXO_##P##1: CHK(OK(1)) R[d] = load_sz<1, false>(ADDR); break;                           \
+    case GXO_##P##2: CHK(OK(2)) R[d] = load_sz<2, false>(ADDR); break;                           \
+    case GXO_##P##4: CHK(OK(4)) R[d] = load_sz<4, false>(ADDR); break;                           \
+    case GXO_##P##8: CHK(OK(8)) R[d] = load_sz<8, false>(ADDR); break;                           \
+    case GXO_##P##S1: CHK(OK(1)) R[d] = load_sz<1, true>(ADDR); break;                           \
+    case GXO_##P##S2: CHK(OK(2)) R[d] = load_sz<2, true>(ADDR); break;                           \
+    case GXO_##P##S4: CHK(OK(4)) R[d] = load_sz<4, true>(ADDR); break;
+
+#define ST_FORM(P, ADDR, VAL, OK)                                                                \
+    case GXO_##P##1: CHK(OK(1)) store_sz<1>(ADDR, VAL); break;                                   \
+    case GXO_##P##2: CHK(OK(2)) store_sz<2>(ADDR, VAL); break;                                   \
+    case GXO_##P##4: CHK(OK(4)) store_sz<4>(ADDR, VAL); break;                                   \
+    case GXO_##P##8: CHK(OK(8)) store_sz<8>(ADDR, VAL); break;
 
 /* atomics at ADDR with the value in R[s]: plain (warp-aggregated), fetching, xchg, cmpxchg */
-#define ATOM_FORM(P, ADDR)                                                                       \
-    case GXO_##P##ADD4: agg_update<AG_ADD, 4>(ADDR, R[s], exec); break;                          \
-    case GXO_##P##OR4: agg_update<AG_OR, 4>(ADDR, R[s], exec); break;                            \
-    case GXO_##P##AND4: agg_update<AG_AND, 4>(ADDR, R[s], exec); break;                          \
-    case GXO_##P##XOR4: agg_update<AG_XOR, 4>(ADDR, R[s], exec); break;                          \
-    case GXO_##P##ADD8: agg_update<AG_ADD, 8>(ADDR, R[s], exec); break;                          \
-    case GXO_##P##OR8: agg_update<AG_OR, 8>(ADDR, R[s], exec); break;                            \
-    case GXO_##P##AND8: agg_update<AG_AND, 8>(ADDR, R[s], exec); break;                          \
-    case GXO_##P##XOR8: agg_update<AG_XOR, 8>(ADDR, R[s], exec); break;                          \
-    case GXO_##P##FADD4: R[s] = fetch_update<AG_ADD, 4>(ADDR, R[s]); break;                      \
-    case GXO_##P##FOR4: R[s] = fetch_update<AG_OR, 4>(ADDR, R[s]); break;                        \
-    case GXO_##P##FAND4: R[s] = fetch_update<AG_AND, 4>(ADDR, R[s]); break;                      \
-    case GXO_##P##FXOR4: R[s] = fetch_update<AG_XOR, 4>(ADDR, R[s]); break;                      \
-    case GXO_##P##FADD8: R[s] = fetch_update<AG_ADD, 8>(ADDR, R[s]); break;                      \
-    case GXO_##P##FOR8: R[s] = fetch_update<AG_OR, 8>(ADDR, R[s]); break;                        \
-    case GXO_##P##FAND8: R[s] = fetch_update<AG_AND, 8>(ADDR, R[s]); break;                      \
-    case GXO_##P##FXOR8: R[s] = fetch_update<AG_XOR, 8>(ADDR, R[s]); break;                      \
-    case GXO_##P##XCHG4: R[s] = xchg<4>(ADDR, R[s]); break;                                      \
-    case GXO_##P##XCHG8: R[s] = xchg<8>(ADDR, R[s]); break;                                      \
-    case GXO_##P##CMPX4: R[0] = cmpxchg<4>(ADDR, R[0], R[s]); break;                             \
-    case GXO_##P##CMPX8: R[0] = cmpxchg<8>(ADDR, R[0], R[s]); break;
+#define ATOM_FORM(P, ADDR, OK)                                                                       \
+    case GXO_##P##ADD4: CHK(OK(4)) agg_update<AG_ADD, 4>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##OR4: CHK(OK(4)) agg_update<AG_OR, 4>(ADDR, R[s], exec); break;                            \
+    case GXO_##P##AND4: CHK(OK(4)) agg_update<AG_AND, 4>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##XOR4: CHK(OK(4)) agg_update<AG_XOR, 4>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##ADD8: CHK(OK(8)) agg_update<AG_ADD, 8>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##OR8: CHK(OK(8)) agg_update<AG_OR, 8>(ADDR, R[s], exec); break;                            \
+    case GXO_##P##AND8: CHK(OK(8)) agg_update<AG_AND, 8>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##XOR8: CHK(OK(8)) agg_update<AG_XOR, 8>(ADDR, R[s], exec); break;                          \
+    case GXO_##P##FADD4: CHK(OK(4)) R[s] = fetch_update<AG_ADD, 4>(ADDR, R[s]); break;                      \
+    case GXO_##P##FOR4: CHK(OK(4)) R[s] = fetch_update<AG_OR, 4>(ADDR, R[s]); break;                        \
+    case GXO_##P##FAND4: CHK(OK(4)) R[s] = fetch_update<AG_AND, 4>(ADDR, R[s]); break;                      \
+    case GXO_##P##FXOR4: CHK(OK(4)) R[s] = fetch_update<AG_XOR, 4>(ADDR, R[s]); break;                      \
+    case GXO_##P##FADD8: CHK(OK(8)) R[s] = fetch_update<AG_ADD, 8>(ADDR, R[s]); break;                      \
+    case GXO_##P##FOR8: CHK(OK(8)) R[s] = fetch_update<AG_OR, 8>(ADDR, R[s]); break;                        \
+    case GXO_##P##FAND8: CHK(OK(8)) R[s] = fetch_update<AG_AND, 8>(ADDR, R[s]); break;                      \
+    case GXO_##P##FXOR8: CHK(OK(8)) R[s] = fetch_update<AG_XOR, 8>(ADDR, R[s]); break;                      \
+    case GXO_##P##XCHG4: CHK(OK(4)) R[s] = xchg<4>(ADDR, R[s]); break;                                      \
+    case GXO_##P##XCHG8: CHK(OK(8)) R[s] = xchg<8>(ADDR, R[s]); break;                                      \
+    case GXO_##P##CMPX4: CHK(OK(4)) R[0] = cmpxchg<4>(ADDR, R[0], R[s]); break;                             \
+    case GXO_##P##CMPX8: CHK(OK(8)) R[0] = cmpxchg<8>(ADDR, R[0], R[s]); break;
 
 /*
  * Interpret one event per lane.  All 32 lanes of the warp call this together; lanes
@@ -106,6 +120,7 @@ namespace gx {
  * "min-pc" mode (only lanes at the smallest pc advance), which re-converges
  * forward-branching code at its join points.
  */
+template <bool CHECKED>
 __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool valid, u64 ev_idx) {
     const u32 lane = lane_id();
     u64 stack[GX_STACK_BYTES / 8];
@@ -116,14 +131,15 @@ __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool vali
     const ulonglong2 *uops = (const ulonglong2 *)env.uops;
     u32 pc = valid ? 0u : PC_DONE;
     u32 exec = __ballot_sync(FULLM, valid);
-    bool div = exec != FULLM;
+    /* the checked build stays in min-pc mode: a lane may stop on its own at any access */
+    bool div = CHECKED || exec != FULLM;
     u64 back = 0;
     for (;;) {
         if (div) {
             const u32 mpc = __reduce_min_sync(FULLM, pc);
             if (mpc == PC_DONE) break;
             exec = __ballot_sync(FULLM, pc == mpc);
-            if (exec == FULLM) div = false;
+            if (!CHECKED && exec == FULLM) div = false;
             if (pc != mpc) continue;
         }
         const ulonglong2 u = uops[pc];
@@ -164,36 +180,54 @@ __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool vali
             continue;
         case GXO_NOP: break;
             /* ctx word k of this lane lives at ctxw[k * env.ctx_row + lane]; aux is the byte offset */
-            LD_FORM(LDC, (const uint8_t *)(ctxw + (aux >> 3) * env.ctx_row + lane) + (aux & 7))
-            LD_FORM(LDS, (const uint8_t *)stack + aux)
-            LD_FORM(LDM, (const uint8_t *)(R[s] + (u64)(s64)imm))
-            ST_FORM(STIS, (uint8_t *)stack + aux, (u64)(s64)imm)
-            ST_FORM(STIM, (uint8_t *)(R[d] + (u64)(s64)(int16_t)aux), (u64)(s64)imm)
-            ST_FORM(STXS, (uint8_t *)stack + aux, R[s])
-            ST_FORM(STXM, (uint8_t *)(R[d] + (u64)(s64)imm), R[s])
-            ATOM_FORM(AS_, (u64)((uint8_t *)stack + aux))
-            ATOM_FORM(AM_, R[d] + (u64)(s64)imm)
-        case GXO_CALL_LOOKUP: R[0] = map_lookup(env.maps[R[1]], (const uint8_t *)R[2], exec, env.stats); break;
+            LD_FORM(LDC, (const uint8_t *)(ctxw + (aux >> 3) * env.ctx_row + lane) + (aux & 7), CTX_OK)
+            LD_FORM(LDS, (const uint8_t *)stack + aux, STK_OK)
+            LD_FORM(LDM, (const uint8_t *)(R[s] + (u64)(s64)imm), LDM_OK)
+            ST_FORM(STIS, (uint8_t *)stack + aux, (u64)(s64)imm, STK_OK)
+            ST_FORM(STIM, (uint8_t *)(R[d] + (u64)(s64)(int16_t)aux), (u64)(s64)imm, STIM_OK)
+            ST_FORM(STXS, (uint8_t *)stack + aux, R[s], STK_OK)
+            ST_FORM(STXM, (uint8_t *)(R[d] + (u64)(s64)imm), R[s], DIMM_OK)
+            ATOM_FORM(AS_, (u64)((uint8_t *)stack + aux), STK_OK)
+            ATOM_FORM(AM_, R[d] + (u64)(s64)imm, DIMM_OK)
+        case GXO_CALL_LOOKUP:
+            CHK(MAP_OK(R[1]) && RANGE_OK(R[2], env.maps[R[1]].key_size))
+            R[0] = map_lookup(env.maps[R[1]], (const uint8_t *)R[2], exec, env.stats);
+            break;
         case GXO_CALL_UPDATE:
+            CHK(MAP_OK(R[1]) && RANGE_OK(R[2], env.maps[R[1]].key_size) && RANGE_OK(R[3], env.maps[R[1]].value_size))
             R[0] = (u64)(s64)map_update(env.maps[R[1]], (const uint8_t *)R[2], (const uint8_t *)R[3], R[4], exec,
                                         env.stats);
             break;
         case GXO_CALL_DELETE: {
+            CHK(MAP_OK(R[1]) && RANGE_OK(R[2], env.maps[R[1]].key_size))
             const gx_dmap &m = env.maps[R[1]];
             R[0] = (u64)(s64)(m.type == GX_MAP_HASH ? hash_delete(m, (const uint8_t *)R[2], env.stats) : GX_EINVAL);
             break;
         }
-        case GXO_CALL_RB_RESERVE: R[0] = rb_reserve(env.maps[R[1]], R[2], exec, ev_idx); break;
+        case GXO_CALL_RB_RESERVE:
+            CHK(RING_OK(R[1]))
+            R[0] = rb_reserve(env.maps[R[1]], R[2], exec, ev_idx);
+            break;
         case GXO_CALL_RB_OUTPUT: {
+            CHK(RING_OK(R[1]) && RANGE_OK(R[2], R[3]))
             const u64 p = rb_reserve(env.maps[R[1]], R[3], exec, ev_idx);
             if (p) copy_bytes((uint8_t *)p, (const uint8_t *)R[2], (u32)R[3]);
             R[0] = p ? 0 : (u64)(s64)GX_EAGAIN;
             break;
         }
         case GXO_CALL_RB_SUBMIT: break; /* records are committed when reserved */
-        case GXO_CALL_RB_DISCARD: ((u32 *)(R[1] - GX_RB_HDR))[1] = GX_RB_DISCARDED; break;
-        case GXO_CALL_AMAX: agg_update<AG_MAX, 8>(R[1], R[2], exec); break;
-        case GXO_CALL_AMIN: agg_update<AG_MIN, 8>(R[1], R[2], exec); break;
+        case GXO_CALL_RB_DISCARD:
+            CHK(MEM_OK(R[1] - GX_RB_HDR + 4, 4))
+            ((u32 *)(R[1] - GX_RB_HDR))[1] = GX_RB_DISCARDED;
+            break;
+        case GXO_CALL_AMAX:
+            CHK(MEM_OK(R[1], 8))
+            agg_update<AG_MAX, 8>(R[1], R[2], exec);
+            break;
+        case GXO_CALL_AMIN:
+            CHK(MEM_OK(R[1], 8))
+            agg_update<AG_MIN, 8>(R[1], R[2], exec);
+            break;
         default:
             set_status(env.stats, GX_E_DEVICE);
             R[0] = 0;
@@ -219,6 +253,12 @@ __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool vali
         R[0] = 0;
         pc = PC_DONE;
         if (!div) break;
+        continue;
+    fault: /* checked build only (div is always set there): this lane's event stops */
+        atomicCAS(&env.stats[GX_STAT_FAULT], 0ull, (u64)pc + 1);
+        set_status(env.stats, GX_E_FAULT);
+        R[0] = 0;
+        pc = PC_DONE;
     }
 finished:
     return R[0];
@@ -227,7 +267,14 @@ finished:
 /* ------------------------------------------------------------------ kernels */
 __global__ void __launch_bounds__(256, 3) gx_exec_kernel(ExecParams P) {
     exec_tiles(P, [](const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {
-        return interp(env, ctxw, valid, ev_idx);
+        return interp<false>(env, ctxw, valid, ev_idx);
+    });
+}
+
+/* the checked build (GX_PROG_CHECKED): every access tested against the event's regions */
+__global__ void __launch_bounds__(256, 3) gx_exec_kernel_checked(ExecParams P) {
+    exec_tiles(P, [](const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {
+        return interp<true>(env, ctxw, valid, ev_idx);
     });
 }
 
@@ -258,15 +305,20 @@ __global__ void gx_hash_insert_kernel(gx_dmap m, const uint8_t *in, u64 npairs, 
 
 /* ------------------------------------------------------------------ host launchers */
 cudaError_t exec_set_smem(size_t bytes) {
-    return cudaFuncSetAttribute(gx_exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(gx_exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gx_exec_kernel_checked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
 }
 
-cudaError_t exec_occupancy(int block, size_t smem, int *blocks_per_sm) {
+cudaError_t exec_occupancy(int block, size_t smem, int *blocks_per_sm, bool checked) {
+    if (checked) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, gx_exec_kernel_checked, block, smem);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, gx_exec_kernel, block, smem);
 }
 
-cudaError_t launch_exec(const ExecParams &p, unsigned grid, unsigned block, size_t smem, cudaStream_t s) {
-    gx_exec_kernel<<<grid, block, smem, s>>>(p);
+cudaError_t launch_exec(const ExecParams &p, unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool checked) {
+    if (checked) gx_exec_kernel_checked<<<grid, block, smem, s>>>(p);
+    else gx_exec_kernel<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 

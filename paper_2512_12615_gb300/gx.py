@@ -21,6 +21,7 @@ from . import _build
 OK = 0
 ENOENT, E2BIG, EAGAIN, ENOMEM, EFAULT, EEXIST, EINVAL, ENOSPC = -2, -7, -11, -12, -14, -17, -22, -28
 E_VERIFY, E_CUDA, E_BUDGET, E_TIMEOUT, E_DEVICE, E_ADMISSION, E_NODEV = -1000, -1001, -1002, -1003, -1004, -1005, -1006
+E_FAULT = -1007  # a checked program's access outside its regions was stopped
 MAP_HASH, MAP_ARRAY, MAP_RINGBUF = 1, 2, 27
 ANY, NOEXIST, EXIST = 0, 1, 2
 
@@ -95,7 +96,7 @@ def _launch(launch) -> Optional[Launch]:
 
 
 class RunStats(ctypes.Structure):
-    _fields_ = [("status", i32), ("reserved", u32), ("budget_trips", u64), ("waits_expired", u64),
+    _fields_ = [("status", i32), ("fault_pc", u32), ("budget_trips", u64), ("waits_expired", u64),
                 ("launches", u64)]
 
 
@@ -359,6 +360,7 @@ def merge_ops(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, map_i
 
 
 PROG_JIT = 1
+PROG_CHECKED = 2  # the checked interpreter: every access tested against the event's regions
 
 
 def jit_check(insns: np.ndarray, map_specs: Sequence[dict], ctx_size: int, deterministic: bool = False,
@@ -466,13 +468,14 @@ class Map:
 class Program:
     def __init__(self, ctx: Context, insns: np.ndarray, maps: Sequence[Map], ctx_size: int,
                  deterministic: bool = False, insn_budget: int = 0, jit: bool = False,
-                 simt: Optional[dict] = None) -> None:
+                 simt: Optional[dict] = None, checked: bool = False) -> None:
         """simt: load the warp-level form (gx_verify_load_simt) with these gx_simt_spec fields:
         uniform (ctx_size flags) and optionally max_insns, max_helper_calls, max_mem_ops;
-        it needs jit=True."""
+        it needs jit=True.  checked: run through the checked interpreter (GX_PROG_CHECKED)."""
         insns = np.ascontiguousarray(insns, dtype=np.uint64)
         arr = (ctypes.c_void_p * max(1, len(maps)))(*[m.h for m in maps])
-        opts = ProgOpts(ctx_size, int(deterministic), insn_budget, PROG_JIT if jit else 0, 0)
+        opts = ProgOpts(ctx_size, int(deterministic), insn_budget, (PROG_JIT if jit else 0) | (PROG_CHECKED if checked else 0),
+                        0)
         log = ctypes.create_string_buffer(8192)
         h = ctypes.c_void_p()
         if simt is None:

@@ -77,7 +77,7 @@ def assert_same(gpu_snap, ora_snap) -> None:
 
 def run_both(ctx: gx.Context, prog: np.ndarray, specs: Sequence[dict], ctx_size: int, events: np.ndarray, *,
              det: bool = True, launch: Optional[Tuple[int, ...]] = None, idx_base: int = 0, check_r0: bool = True,
-             jit: bool = False, init: Optional[Sequence[Optional[bytes]]] = None):
+             jit: bool = False, init: Optional[Sequence[Optional[bytes]]] = None, checked: bool = False):
     """Returns (gpu snapshot, oracle snapshot, r0 gpu, r0 oracle) after asserting equality.
 
     init: per map, None or the initial values of an array map (max_entries * value_size bytes)."""
@@ -95,13 +95,13 @@ def run_both(ctx: gx.Context, prog: np.ndarray, specs: Sequence[dict], ctx_size:
     for i, blob in enumerate(init or []):
         if blob is not None:
             gm[i].write(blob)
-    p = gx.Program(ctx, prog, gm, ctx_size, deterministic=det, jit=jit)
+    p = gx.Program(ctx, prog, gm, ctx_size, deterministic=det, jit=jit, checked=checked)
     dev = device_events(events)
     ret = torch.zeros(max(n, 1), dtype=torch.int64, device="cuda")
     p.run(dev, n, ret_out=ret, idx_base=idx_base, launch=launch)
     torch.cuda.synchronize()
     st = p.status()
-    assert st.status == 0, st.status
+    assert st.status == 0 and st.fault_pc == 0, (st.status, st.fault_pc)
     r0_g = ret[:n].cpu().numpy()
     gs, os_ = snapshot_gpu(gm), snapshot_oracle(om)
     if check_r0:
