@@ -616,6 +616,7 @@ int gx_verify_load(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *const *
             p->jp.ctx_size = opts->ctx_size;
             p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
             if (opts->flags & GX_PROG_JIT) {
+                p->jp.max_path = path_bound(insns, n, specs.data(), n_maps, *opts);
                 rc = jit_build({&p->jp}, p->jk, msg);
                 p->jit = rc == GX_OK;
             }
@@ -742,6 +743,7 @@ int gx_verify_load_simt(gx_ctx *c, const uint64_t *insns, uint32_t n, gx_map *co
         p->jp.use = v.map_use;
         p->jp.ctx_size = opts->ctx_size;
         p->jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        p->jp.max_path = v.simt.max_insns; /* the SIMT pass counted every path */
         p->jp.warp = true;
         rc = jit_build({&p->jp}, p->jk, msg);
         p->jit = rc == GX_OK;

@@ -20,6 +20,9 @@ struct JitProgram {
     std::vector<MapUse> use;       /* per map: may its updates be combined per block? */
     uint32_t ctx_size = 8;         /* bytes per event record */
     uint64_t budget = 1ull << 16;
+    /* the longest path's instruction count, from the verifier (0: unknown); when it is
+       within `budget`, no event can reach the back-jump budget and the check is left out */
+    uint64_t max_path = 0;
     bool warp = false; /* a SIMT-verified warp-level handler: shared effects once per warp, by its leader lane */
 };
 
@@ -66,6 +69,9 @@ struct ShardPlan {
     }
 };
 ShardPlan plan_shards(const JitProgram &p);
+/* the verifier's bound on any path's instruction count (0 if it cannot give one) */
+uint64_t path_bound(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                    const gx_prog_opts &opts);
 
 /*
  * compile (or fetch from the caches) one kernel running progs[slot] for chunk slot `slot`;

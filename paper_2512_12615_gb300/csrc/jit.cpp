@@ -463,10 +463,13 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         return lo < GX_STACK_BYTES ? stk_materialise(lo) : "";
     };
     const uint64_t budget = p.budget;
+    /* every path is shorter than the budget: no event can reach it, so no counting */
+    const bool bounded = p.max_path && p.max_path <= budget;
     auto jump = [&](uint32_t pc, int64_t tgt) -> std::string {
         if (structured) return "nb_ = " + std::to_string(tgt) + "u;";
         std::string g = "goto L" + std::to_string(tgt) + ";";
-        if (tgt <= (int64_t)pc) return "{ if (++back > " + std::to_string(budget) + "ull) goto budget_trip; " + g + " }";
+        if (tgt <= (int64_t)pc && !bounded)
+            return "{ if (++back > " + std::to_string(budget) + "ull) goto budget_trip; " + g + " }";
         return g;
     };
     bool block_ends = false; /* structured: the open block's last statement left it (jump or exit) */
@@ -1020,6 +1023,20 @@ int jit_build(const std::vector<const JitProgram *> &progs, JitKernel &out, std:
     return GX_OK;
 }
 
+uint64_t path_bound(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
+                    const gx_prog_opts &opts) {
+    /*
+     * The SIMT pass with every ctx byte uniform accepts what the per-lane verifier accepts,
+     * and it counts each path's instructions, pruning a state only by a kept state whose
+     * count is at least as large: its maximum is the longest path's length.
+     */
+    SimtIn in;
+    in.uniform.assign(opts.ctx_size, 1);
+    VerifyOut v;
+    if (verify_program(insns, n, maps, n_maps, opts, v, &in) != GX_OK) return 0;
+    return v.simt.max_insns;
+}
+
 int check_sched_program(const uint64_t *insns, uint32_t n, const gx_map_spec *maps, uint32_t n_maps,
                         const gx_prog_opts &opts, const gx_simt_spec *limits, VerifyOut &v) {
     if (opts.ctx_size != GX_SCHED_CTX) {
@@ -1074,6 +1091,7 @@ extern "C" int gx_jit_check(const uint64_t *insns, uint32_t n, const gx_map_spec
         jp.use = v.map_use;
         jp.ctx_size = opts->ctx_size;
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        jp.max_path = gx::path_bound(insns, n, maps, n_maps, *opts);
         const std::string src = gx::jit_source({&jp}, msg, rc);
         std::vector<char> cubin;
         if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);
@@ -1102,6 +1120,7 @@ extern "C" int gx_jit_check_simt(const uint64_t *insns, uint32_t n, const gx_map
         jp.use = v.map_use;
         jp.ctx_size = opts->ctx_size;
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        jp.max_path = v.simt.max_insns;
         jp.warp = true;
         const std::string src = gx::jit_source({&jp}, msg, rc);
         std::vector<char> cubin;
@@ -1135,12 +1154,14 @@ extern "C" int gx_jit_check_sched(const uint64_t *insns, uint32_t n, const gx_ma
         jp.use = v.map_use;
         jp.ctx_size = opts->ctx_size;
         jp.budget = opts->insn_budget ? opts->insn_budget : (1ull << 16);
+        jp.max_path = gx::path_bound(insns, n, maps, n_maps, *opts);
         hp.insns.assign(hook, hook + n_hook);
         hp.info = hv.info;
         hp.maps.assign(hook_maps, hook_maps + n_hook_maps);
         hp.use = hv.map_use;
         hp.ctx_size = hook_opts->ctx_size;
         hp.budget = hook_opts->insn_budget ? hook_opts->insn_budget : (1ull << 16);
+        hp.max_path = gx::path_bound(hook, n_hook, hook_maps, n_hook_maps, *hook_opts);
         const std::string src = gx::jit_source({&jp}, msg, rc, &hp);
         std::vector<char> cubin;
         if (rc == GX_OK) rc = gx::jit_cubin(src, gx::jit_key(src), cubin, msg);
