@@ -300,6 +300,9 @@ std::string gen_wc_flush(const ShardPlan &sp, int slot) {
     return o.str();
 }
 
+/* the longest run of arithmetic a forward jump may skip and still be emitted inline */
+const int64_t FOLD_MAX = 8;
+
 /* a program with more map-update and lookup sites than this calls their slow paths out of line */
 const uint32_t OUTLINE_SITES = 8;
 
@@ -370,6 +373,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
     const uint32_t n = (uint32_t)p.insns.size();
     std::vector<uint8_t> target(n + 1, 0);
     std::vector<uint8_t> leader(n + 1, 0); /* first instruction of a basic block */
+    std::vector<uint32_t> tcount(n + 1, 0); /* jumps to each instruction */
     bool acyclic = true;
     leader[0] = 1;
     for (uint32_t pc = 0; pc < n; pc++) {
@@ -388,6 +392,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             int64_t t = (int64_t)pc + 1 + ((cls == 6 && (op & 0xF0) == 0) ? imm : off);
             target[t] = 1;
             leader[t] = 1;
+            tcount[t]++;
             if (t <= (int64_t)pc) acyclic = false;
         }
     }
@@ -401,6 +406,33 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
      * warp-level handlers (whose lanes never diverge).
      */
     const bool structured = acyclic && !p.warp;
+    /*
+     * A conditional jump forward over a short run of register arithmetic (no memory,
+     * helpers or jumps; reached only by falling through) stays inside its block as
+     * "if (!cond) { run }": predicated code instead of two more blocks and joins.
+     */
+    std::vector<int64_t> fold(n + 1, -1); /* fold[pc]: the target of a jump at pc emitted inline */
+    for (uint32_t pc = 0; structured && pc < n; pc++) {
+        if (!p.info[pc].visited) continue;
+        const uint64_t w = p.insns[pc];
+        const int op = (int)(w & 0xFF), cls = op & 7, code = op & 0xF0;
+        if (op == 0x18) {
+            pc++;
+            continue;
+        }
+        if ((cls != 5 && cls != 6) || code == 0x00 || code == 0x80 || code == 0x90) continue;
+        const int64_t t = (int64_t)pc + 1 + (int)(int16_t)(uint16_t)((w >> 16) & 0xFFFF);
+        if (t <= (int64_t)pc + 1 || t - pc - 1 > FOLD_MAX) continue;
+        bool ok = true;
+        for (int64_t k = pc + 1; k < t && ok; k++) {
+            const int kc = (int)(p.insns[k] & 7);
+            ok = p.info[k].visited && (kc == 4 || kc == 7) && tcount[k] == 0;
+        }
+        if (!ok) continue;
+        fold[pc] = t;
+        leader[pc + 1] = 0;
+        if (tcount[t] == 1) leader[t] = 0; /* its other way in is falling through the run */
+    }
     /*
      * Many map-update and lookup sites: their slow paths (device-memory updates, the
      * ordered hash probe) go out of line, so that a long program's code fits the
@@ -473,6 +505,7 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         return g;
     };
     bool block_ends = false; /* structured: the open block's last statement left it (jump or exit) */
+    int64_t fold_end = -1;   /* structured: the end of an inline "if (!cond) { run }" */
     for (uint32_t pc = 0; pc < n; pc++) {
         const InsnInfo &ii = p.info[pc];
         uint64_t w = p.insns[pc];
@@ -480,6 +513,10 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
         int dst = (int)((w >> 8) & 0xF), src = (int)((w >> 12) & 0xF);
         int off = (int)(int16_t)(uint16_t)((w >> 16) & 0xFFFF);
         int32_t imm = (int32_t)(uint32_t)(w >> 32);
+        if ((int64_t)pc == fold_end) {
+            o << "  }\n";
+            fold_end = -1;
+        }
         if (structured && leader[pc] && ii.visited) {
             if (pc) o << (block_ends ? "  }\n" : "  nb_ = " + std::to_string(pc) + "u; }\n") << "  __syncwarp(vm_);\n";
             o << "  if (nb_ == " << pc << "u) {\n";
@@ -632,6 +669,11 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             bool w32 = cls == 6, x = op & 8;
             std::string s = x ? R(src) : (w32 ? hex64((uint32_t)imm) : hex64((uint64_t)(int64_t)imm));
             int64_t t = (int64_t)pc + 1 + off;
+            if (structured && fold[pc] >= 0) {
+                o << "if (!" << (w32 ? "c32<" : "c64<") << c << ">(" << R(dst) << ", " << s << ")) {";
+                fold_end = t;
+                break;
+            }
             if (structured) {
                 o << "nb_ = " << (w32 ? "c32<" : "c64<") << c << ">(" << R(dst) << ", " << s << ") ? " << t << "u : "
                   << pc + 1 << "u;";
