@@ -73,7 +73,23 @@ int decode_program(const uint64_t *insns, uint32_t n, const VerifyOut &v, std::v
     static_assert(GXO_J64X_JEQ - GXO_J64K_JEQ == 11 && GXO_J32X_JEQ - GXO_J64K_JEQ == 33, "jump op order");
     static_assert(GXO_LDSS4 - GXO_LDS1 == 6 && GXO_AM_ADD4 - GXO_AS_ADD4 == 20, "memory op order");
     static_assert(GX_NUM_OPS <= 256, "operation field");
+    static_assert(GXO_F64K_MOV - GXO_F64K_ADD == 13, "fused op order");
     uops.assign((size_t)n * 2, 0);
+    /* instructions some jump lands on: a fused pair may not have its second one among them */
+    std::vector<uint8_t> landed(n + 1, 0);
+    for (uint32_t pc = 0; pc < n; pc++) {
+        const uint64_t w = insns[pc];
+        const int op = (int)(w & 0xFF), cls = op & 7, code = op & 0xF0;
+        if (op == 0x18) {
+            pc++;
+            continue;
+        }
+        if ((cls == 5 || cls == 6) && code != 0x80 && code != 0x90) {
+            const int64_t t = (int64_t)pc + 1 + ((cls == 6 && code == 0) ? (int32_t)(uint32_t)(w >> 32)
+                                                                           : (int)(int16_t)(uint16_t)((w >> 16) & 0xFFFF));
+            if (t >= 0 && t <= (int64_t)n) landed[t] = 1;
+        }
+    }
     /* one micro-op per instruction slot: micro-op k is instruction k, so jump targets stay */
     for (uint32_t pc = 0; pc < n; pc++) {
         const uint64_t w = insns[pc];
@@ -119,6 +135,20 @@ int decode_program(const uint64_t *insns, uint32_t n, const VerifyOut &v, std::v
             }
             const int a = alu_index(code, (code == 0x30 || code == 0x90) ? off : 0);
             if (a < 0) return bad("unknown ALU operation");
+            /* "mov d, s" then a 64-bit immediate operation on d, nothing jumping between them:
+               one micro-op d = op(s, imm) that skips the second */
+            if (op == 0xBF && !off && pc + 1 < n && !landed[pc + 1] && v.info[pc + 1].visited) {
+                const uint64_t w2 = insns[pc + 1];
+                const int op2 = (int)(w2 & 0xFF), code2 = op2 & 0xF0;
+                const int off2 = (int)(int16_t)(uint16_t)((w2 >> 16) & 0xFFFF);
+                const int a2 = (op2 & 0x0F) == 0x07 && code2 != 0xD0 && code2 != 0x80
+                                   ? alu_index(code2, (code2 == 0x30 || code2 == 0x90) ? off2 : 0)
+                                   : -1;
+                if (a2 >= 0 && a2 != 13 && (int)((w2 >> 8) & 0xF) == dst && !(code2 == 0xB0 && off2)) {
+                    emit(GXO_F64K_ADD + a2, 0, (int32_t)(uint32_t)(w2 >> 32));
+                    break;
+                }
+            }
             emit(GXO_A64K_ADD + ((w32 ? 2 : 0) + (x ? 1 : 0)) * 14 + a, 0, imm);
             break;
         }

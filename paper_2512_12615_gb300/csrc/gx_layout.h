@@ -27,7 +27,10 @@
  * operations, in enum order (O_ADD .. O_MOV of the device header); jumps: the 11
  * conditions x (64 K, 64 X, 32 K, 32 X); loads: region (C ctx, S stack, M memory) x size
  * (1, 2, 4, 8, then sign-extending 1, 2, 4); stores: region (S, M) x size, immediate or
- * register; atomics: region (S, M) x the 20 forms; then the helper calls.
+ * register; atomics: region (S, M) x the 20 forms; then the helper calls.  F64K_*: a
+ * register copy fused with the 64-bit immediate operation on its destination that
+ * follows it ("mov d, s; op d, imm" as d = op(s, imm)), which then skips that second
+ * instruction's micro-op (left in place for jumps to it).
  */
 #define GX_ALU_OPS(X, P) X(P##ADD) X(P##SUB) X(P##MUL) X(P##DIV) X(P##SDIV) X(P##MOD) X(P##SMOD) \
     X(P##OR) X(P##AND) X(P##XOR) X(P##LSH) X(P##RSH) X(P##ARSH) X(P##MOV)
@@ -43,6 +46,7 @@
     GX_ALU_OPS(X, A64K_) GX_ALU_OPS(X, A64X_) GX_ALU_OPS(X, A32K_) GX_ALU_OPS(X, A32X_)          \
     X(NEG64) X(NEG32) X(MOVSX64_8) X(MOVSX64_16) X(MOVSX64_32) X(MOVSX32_8) X(MOVSX32_16)        \
     X(LE16) X(LE32) X(BSWAP16) X(BSWAP32) X(BSWAP64) X(LDIMM64)                                   \
+    GX_ALU_OPS(X, F64K_)                                                                         \
     GX_JMP_OPS(X, J64K_) GX_JMP_OPS(X, J64X_) GX_JMP_OPS(X, J32K_) GX_JMP_OPS(X, J32X_)          \
     X(JA) X(EXIT) X(NOP)                                                                         \
     GX_LD_OPS(X, LDC) GX_LD_OPS(X, LDS) GX_LD_OPS(X, LDM)                                        \

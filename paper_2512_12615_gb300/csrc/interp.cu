@@ -169,6 +169,13 @@ __device__ __noinline__ u64 interp(const ExecEnv env, const u64 *ctxw, bool vali
             break;
         }
         case GXO_LDIMM64: R[d] = u.y; break;
+            /* "mov d, s; op d, imm": d = op(s, imm), then past the second instruction */
+#define FUSED_CASE(NAME, O) \
+    case GXO_F64K_##NAME: R[d] = a64<O>(R[s], (u64)(s64)imm); pc += 2; continue;
+            FUSED_CASE(ADD, O_ADD) FUSED_CASE(SUB, O_SUB) FUSED_CASE(MUL, O_MUL) FUSED_CASE(DIV, O_DIV)
+            FUSED_CASE(SDIV, O_SDIV) FUSED_CASE(MOD, O_MOD) FUSED_CASE(SMOD, O_SMOD) FUSED_CASE(OR, O_OR)
+            FUSED_CASE(AND, O_AND) FUSED_CASE(XOR, O_XOR) FUSED_CASE(LSH, O_LSH) FUSED_CASE(RSH, O_RSH)
+            FUSED_CASE(ARSH, O_ARSH) FUSED_CASE(MOV, O_MOV)
             JMP_FORM(J64K_, c64, (u64)(s64)imm)
             JMP_FORM(J64X_, c64, R[s])
             JMP_FORM(J32K_, c32, (u64)(u32)imm)
