@@ -55,6 +55,7 @@ struct ShardMap {
     uint32_t max_bits = 0;   /* cache: log2 entries at most */
     uint32_t n_values = 0;   /* full: max_entries */
     std::vector<uint8_t> op; /* per 4-byte word of a value: UpdClass | UC_W8 */
+    uint32_t sites = 0;      /* update instructions that reach it at a known offset */
 };
 struct ShardPlan {
     std::vector<ShardMap> maps; /* private copies first, then caches */

@@ -183,9 +183,12 @@ ShardPlan plan_shards(const JitProgram &p) {
     ShardPlan plan;
     /* only maps that some update instruction reaches with a known offset are worth a shard */
     std::vector<bool> targeted(p.maps.size(), false);
+    std::vector<uint32_t> sites(p.maps.size(), 0);
     for (const InsnInfo &ii : p.info)
-        if (ii.visited && ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES && ii.vmap < (int)targeted.size())
+        if (ii.visited && ii.vmap >= 0 && ii.voff >= 0 && ii.voff < InsnInfo::ARG_VARIES && ii.vmap < (int)targeted.size()) {
             targeted[ii.vmap] = true;
+            sites[ii.vmap]++;
+        }
     /* private copies first (fixed offsets), then the caches (offsets follow the runtime width) */
     std::vector<ShardMap> caches;
     uint32_t off = 0, cache_max = 0;
@@ -197,6 +200,7 @@ ShardPlan plan_shards(const JitProgram &p) {
         sm.map = (int)m;
         sm.stride = (ms.value_size + 7u) & ~7u;
         sm.op = p.use[m].op;
+        sm.sites = sites[m];
         const uint64_t full_bytes = (uint64_t)ms.max_entries * sm.stride;
         if (ms.type == GX_MAP_ARRAY && full_bytes <= WC_FULL_MAX && sm.stride <= 256) {
             const uint32_t need = up16((uint32_t)full_bytes);
@@ -322,9 +326,17 @@ std::string gen_update(const ShardPlan &sp, const InsnInfo &ii, const char *op, 
         o << "sh_update" << t << "(sh_addr(env.shard + " << sm->acc_off << ") + (u32)(a_ - (u64)env.maps[" << sm->map
           << "].values), " << val << "); ";
     } else {
-        o << "uint8_t *e_ = wc_entry(env.shard + " << cache_off(sp, k) << ", " << cache_bits(*sm) << ", "
-          << 8 + sm->stride << "u, a_ - " << ii.voff << "ull); "
-          << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); ";
+        const std::string look = "wc_entry(env.shard + " + cache_off(sp, k) + ", " + cache_bits(*sm) + ", " +
+                                 std::to_string(8 + sm->stride) + "u, a_ - " + std::to_string(ii.voff) + "ull)";
+        if (sm->sites > 1) {
+            /* the event's last entry of this cache is reused for another word of the same value */
+            const std::string kb = "wcb" + std::to_string(k), ke = "wce" + std::to_string(k);
+            o << "uint8_t *e_ = " << ke << "; if (a_ - " << ii.voff << "ull != " << kb << ") { e_ = " << look << "; " << kb
+              << " = a_ - " << ii.voff << "ull; " << ke << " = e_; } ";
+        } else {
+            o << "uint8_t *e_ = " << look << "; ";
+        }
+        o << "if (e_) sh_update" << t << "(sh_addr(e_) + " << ii.voff << "u, " << val << "); ";
         if (outline)
             o << "else dev_update" << t << "(a_, " << val << ", env.wc_agg); ";
         else
@@ -483,6 +495,15 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
       << "  u64 back = 0;\n"
       << "  (void)lane; (void)ev_idx; (void)back; (void)r10;\n";
     if (structured) o << "  u32 nb_ = 0;\n";
+    /*
+     * Per cache: the value base and entry of the event's last cache lookup.  An entry holds
+     * one value from its claim until the block's flush, so a lookup (or its miss) for the
+     * same value stays valid for the rest of the event.  1 is no value's base.
+     */
+    for (size_t k = 0; k < sp.maps.size(); k++)
+        if (!sp.maps[k].full && sp.maps[k].sites > 1)
+            o << "  u64 wcb" << k << " = 1ull; uint8_t *wce" << k << " = nullptr; (void)wcb" << k << "; (void)wce" << k
+              << ";\n";
     /* before a helper that reads stack memory through R2 / R3 */
     auto mat = [&](const InsnInfo &ii, bool r3_mem) -> std::string {
         if (!scalar) return "";
