@@ -272,7 +272,13 @@ finished:
 }
 
 /* ------------------------------------------------------------------ kernels */
-__global__ void __launch_bounds__(256, 3) gx_exec_kernel(ExecParams P) {
+/*
+ * Five blocks of 256 per SM (48 registers): the interpreter waits on its micro-op, register
+ * and stack loads more than it computes, so more resident warps pay for the spills the
+ * cap brings (three blocks ran page-heat 1.2 times and latency 1.3 times slower; eight
+ * blocks, at 32 registers, 2 to 3 times slower).
+ */
+__global__ void __launch_bounds__(256, 5) gx_exec_kernel(ExecParams P) {
     exec_tiles(P, [](const ExecEnv &env, const u64 *ctxw, bool valid, u64 ev_idx) {
         return interp<false>(env, ctxw, valid, ev_idx);
     });
