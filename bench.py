@@ -46,7 +46,7 @@ SEED = 0x6758
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a 16M-event launch; traffic grows with the
 # events streamed, so a launch's traffic is this figure times its events.  Re-take it whenever
 # that kernel changes.
-PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (543.651584e6 + 5.796608e6) / 16777216
+PAGEHEAT_JIT_DRAM_BYTES_PER_EVENT = (543.648768e6 + 5.825792e6) / 16777216
 PAGEHEAT_WORKLOAD = ("page-heat policy, 64M events/GPU, Zipf(1.1) 4 KiB pages over 64 GiB, "
                      "hash map 1M entries (u64 -> {count, last_ts}), 8-trip loop")
 
