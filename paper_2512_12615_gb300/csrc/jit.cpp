@@ -413,8 +413,8 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
      * emitted as a sequence of its basic blocks, block b as "if (nb_ == b) { ...; nb_ =
      * successor; }" with nb_ the lane's next block, and an exit sets nb_ past every block
      * instead of returning.  So every valid lane passes every block boundary, in the same
-     * order, and a __syncwarp over the valid lanes there joins lanes that took different
-     * branches before the next block.  Gotos are kept for programs with loops and for
+     * order, and a __syncwarp over the valid lanes before a block that a jump lands on
+     * joins lanes that took different branches.  Gotos are kept for programs with loops and for
      * warp-level handlers (whose lanes never diverge).
      */
     const bool structured = acyclic && !p.warp;
@@ -539,7 +539,9 @@ int gen_body(const JitProgram &p, const ShardPlan &sp, int slot, std::string &ou
             fold_end = -1;
         }
         if (structured && leader[pc] && ii.visited) {
-            if (pc) o << (block_ends ? "  }\n" : "  nb_ = " + std::to_string(pc) + "u; }\n") << "  __syncwarp(vm_);\n";
+            /* a join only where some jump lands: a block entered by falling through alone has
+               the one way in, so its lanes need no regrouping */
+            if (pc) o << (block_ends ? "  }\n" : "  nb_ = " + std::to_string(pc) + "u; }\n") << (tcount[pc] ? "  __syncwarp(vm_);\n" : "");
             o << "  if (nb_ == " << pc << "u) {\n";
             block_ends = false;
         } else if (!structured && target[pc]) {
