@@ -381,7 +381,9 @@ def run_latency(gx, torch, jit=True, pairs=None):
            "Mevents_per_s": round(2 * pairs / ms / 1e3, 1), "Mpairs_per_s": round(pairs / ms / 1e3, 1),
            "kernel_ms_median": round(ms, 4), "GBps": round(nbytes / ms / 1e6, 1),
            "hbm_frac": round(nbytes / ms / 1e6 / peak, 4), "ringbuf_bytes": len(raw), "dropped": dropped,
-           "launch": dict(zip(("block", "ept", "shards", "variant"), tuned)), "clocks": clk,
+           "launch": {**dict(zip(("block", "ept", "shards", "variant"), tuned)),
+                      "grid": "one block per chunk" if prog.tuned_grid == gx.GRID_PER_CHUNK else "one wave"},
+           "clocks": clk,
            "kernel_ms_all": [round(t, 4) for t in times], "parity": parity}
     prog.destroy()
     for m in maps:

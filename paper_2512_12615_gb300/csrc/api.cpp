@@ -991,13 +991,14 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
         auto rewind = [&] {
             for (auto &r : rings) cudaMemcpyAsync(r.first, r.second, 16, cudaMemcpyDeviceToDevice, s);
         };
-        /* the fastest of `reps` timed launches of l over m events (after one untimed launch), so
-           that one slow launch (a clock step, another stream) does not rank a shape down; < 0 if
-           it cannot launch */
+        /* the median of `reps` timed launches of l over m events (after one untimed launch):
+           one slow launch (a clock step, another stream) does not rank a shape down, and a
+           shape whose launches are only sometimes fast is not ranked up; < 0 if it cannot
+           launch */
         auto timed = [&](const gx_launch &l, uint64_t m, int reps) -> float {
             rewind();
             if (launch_plain(p, (const uint8_t *)timg, img_bytes, events, m, 0, nullptr, l, s)) return -1.0f;
-            float fastest = -1.0f;
+            std::vector<float> t;
             for (int r = 0; r < reps; r++) {
                 rewind();
                 cudaEventRecord(e0, s);
@@ -1006,9 +1007,10 @@ static int autotune_impl(gx_prog *p, const void *events, uint64_t n, cudaStream_
                 cudaEventSynchronize(e1);
                 float ms = 0;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (fastest < 0 || ms < fastest) fastest = ms;
+                t.push_back(ms);
             }
-            return fastest;
+            std::sort(t.begin(), t.end());
+            return t[t.size() / 2];
         };
         std::vector<std::pair<float, gx_launch>> ranked;
         for (uint32_t b : blocks)
