@@ -409,3 +409,16 @@ def test_stealing_source_shape(tmp_path, monkeypatch):
     (plain,) = list((tmp_path / "plain").glob("*.cu"))
     ptext = plain.read_text()
     assert "gx_steal" not in ptext and "gx_sched_call" not in ptext and "exec_steal" not in ptext
+
+
+def test_loop_free_joins_only_where_jumps_land(tmp_path, monkeypatch):
+    """A block entered only by falling through has one way in, so it needs no warp join.
+    The latency program's blocks are the fall-through side of its validation branches,
+    except the shared exit block that every failed check jumps to: one join in all."""
+    monkeypatch.setenv("GX_JIT_DUMP_DIR", str(tmp_path))
+    prog, specs, cs = P.latency()
+    _check(prog, specs, cs)
+    (f,) = list(tmp_path.glob("*.cu"))
+    body = f.read_text().split("} // namespace gx")[0]
+    assert body.count("if (nb_ == ") == 10
+    assert body.count("__syncwarp(vm_)") == 1
