@@ -501,8 +501,9 @@ int gx_last_status(gx_prog *prog, gx_run_stats *out, int reset, void *stream);
  * Pick the launch for (prog, n) by timing candidates on a scratch copy of the program's
  * maps (the real maps, ring buffers included, are not touched): block size, events per
  * thread and, for specialised programs, the map-sharding width and miss policy
- * (gx_launch.shards) and the kernel variant.  Candidates are ranked on the first 64M
- * events; when n is larger the best three are timed again on all n events.  The choice is
+ * (gx_launch.shards) and the kernel variant.  Each candidate's time is the median of three
+ * launches after an untimed one, over the first 64M events; the best three are then timed
+ * again over all n events (the median of five) and the fastest is chosen.  The choice is
  * cached per program and size bucket and used by later runs, and its sharding choice is
  * the program's default in batches and served ticks; *best (nullable) gets it.
  * Synchronous; GX_EINVAL for n == 0 or a null events_dev.
